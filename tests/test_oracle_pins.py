@@ -465,6 +465,84 @@ def test_pgs_single_frictionless_contact_closed_form():
     assert np.allclose(d1["v"], d["v"], atol=1e-13)
 
 
+def _vertices_world(m, q):
+    R, p, _ = O.fk(m, q)
+    out = []
+    for b in range(m.nb):
+        for k in range(8):
+            loc = np.array(m.com[b][:]) + np.array([1 if (k >> i) & 1 else -1 for i in range(3)]) * np.array(m.half[b][:])
+            out.append((b, loc, p[b] + R[b] @ loc))
+    return out
+
+
+def test_pgs_single_contact_on_a_hinged_brick():
+    """A brick on a hinge dips one corner 1 mm into the plane; mu = 0.  The
+    Jacobian of that corner (finite differences of FK, hinge column included)
+    gives lambda = max(0, (t - J v_free) / (A + R)) after one sweep."""
+    m = H.make_model([dict(half=(0.05, 0.05, 0.05), mass=1.0),
+                      dict(parent=0, axis=1, p_fix=(0.05, 0, 0), com=(0.03, 0, 0))])
+    q = free_q((0.0, 0.0, 0.3), quat=np.array([1.0, 0.05, 0.02, 0.0]) / np.linalg.norm([1.0, 0.05, 0.02, 0.0]),
+               hinges=[0.9])
+    verts = _vertices_world(m, q)
+    zs = [x[2][2] for x in verts]
+    k = int(np.argmin(zs))
+    assert verts[k][0] == 1 and sorted(zs)[1] - zs[k] > 0.005
+    q[2] -= zs[k] + 0.001
+    body, local, _ = verts[k]
+    v = np.array([0.05, 0.02, -0.3, 0.2, -0.4, 0.1, -1.5])
+    p = O.default_params(mu=0.0, box_box=0)
+    d = O.step_detail(m, q, v, np.zeros(2 * O.MAXB), prm=p)
+    assert d["nc"] == 1
+    n = O.nv(m)
+    J = np.zeros(n)
+    eps = 1e-7
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        qd = H.qdot_from_v(m, q, e)
+        Rp, pp, _ = O.fk(m, q + eps * qd)
+        Rm, pm, _ = O.fk(m, q - eps * qd)
+        J[i] = ((pp[body] + Rp[body] @ local)[2] - (pm[body] + Rm[body] @ local)[2]) / (2 * eps)
+    assert abs(J[6]) > 0.01
+    M = O.mass_matrix(m, q, p)
+    vfree = d["vfree"]
+    A = J @ np.linalg.solve(M, J)
+    omg = 2 * np.pi / p.soft_tau
+    kden = p.dt * omg * omg + 2 * p.soft_zeta * omg
+    erp = p.dt * omg * omg / kden
+    kappa = 1.0 / (p.dt * kden)
+    t = erp * 0.001 / p.dt
+    lam = max(0.0, (t - J @ vfree) / (A + kappa * A))
+    assert lam > 0
+    assert abs(d["lam"][0, 0] - lam) < 1e-7 * lam
+    assert abs(J @ d["v"][:n] - t + kappa * A * lam) < 1e-8
+
+
+def test_internal_contact_impulses_conserve_momentum():
+    """Box/box contacts inside one robot exchange equal and opposite impulses:
+    the contact part of the velocity change, M (v+ - v_free), has no net
+    linear or angular momentum (rows 0..5 of a free root)."""
+    g = P.grammar(40, seed=3)
+    p = O.default_params(ground=0, gravity=(0, 0, 0), actuate=0)
+    rng = np.random.default_rng(1)
+    seen = 0
+    for i in range(g.n):
+        m = O.model_from_population(g, i)
+        n = O.nv(m)
+        q = g.q0[i, :O.nq(m)].copy()
+        q[7:] = rng.uniform(-1.2, 1.2, n - 6)
+        v = np.zeros(n)
+        d = O.step_detail(m, q, v, np.zeros(2 * O.MAXB), prm=p)
+        if d["nc"] == 0 or np.abs(d["lam"]).max() < 1e-6:
+            continue
+        seen += 1
+        M = O.mass_matrix(m, q, p)
+        dp = M @ (d["v"][:n] - d["vfree"])
+        assert np.abs(dp[:6]).max() < 1e-12 * max(1.0, np.abs(dp).max())
+        assert np.abs(dp[6:]).max() > 1e-6
+    assert seen >= 3
+
+
 def test_resting_cube_steady_penetration():
     """Resting flat cube: per-contact impulse m g dt / 4 and steady depth
     d* = kappa A lambda dt / ERP, with A = 1/m + |r x n|^2 / I for a corner."""
