@@ -1,0 +1,178 @@
+/*
+ * b3sim.h -- C ABI of the B300 population simulator.
+ *
+ * What it computes.  The paper (Sec. 4 "Initial Benchmarking", "Simulation
+ * Parameters"; Sec. 5) times a physics engine that advances many independent
+ * *variants* of a robot scene for a fixed number of steps, on the CPU and on
+ * the GPU, and (Sec. 6) splits the variants between the two.  This library is
+ * that engine for one GPU: every variant is an articulated modular robot (a
+ * core cube plus hinge-jointed cubic bricks, or a single free box) on a
+ * ground plane, and one call advances the whole population by n steps.
+ * Each step, per variant, in this order:
+ *   1. CPG controller: s <- s + dt W s (W antisymmetric from the per-hinge
+ *      weights), hinge torque tau = clamp(kp (theta_max clamp(x,-1,1) - theta)
+ *      - kd theta_dot, -tau_max, tau_max);
+ *   2. forward kinematics down the body tree;
+ *   3. bias forces c(q, v) by recursive Newton-Euler, gravity as base
+ *      acceleration;
+ *   4. joint-space inertia M(q) by the composite-rigid-body algorithm plus a
+ *      hinge armature;
+ *   5. Cholesky M = L L^T and v_free = v + dt M^-1 (tau - c);
+ *   6. contacts: box/plane vertices; box/box separating-axis test with face
+ *      clipping or an edge-edge point; at most contact_cap contacts (the
+ *      deepest, in list order);
+ *   7. soft projected Gauss-Seidel over the contact impulses (ERP/CFM soft
+ *      constraints, disk friction cone, pgs_iters sweeps, list order);
+ *   8. semi-implicit Euler: root position, quaternion exponential map,
+ *      hinge angles.
+ * Fitness is the core's xy displacement since the start of the run.
+ *
+ * Generalized coordinates of a variant with nb bodies (nh = nb - 1 hinges):
+ *   q = (p_root[3], quat_root[4] (w,x,y,z), theta[nh])     nq = nb + 6
+ *   v = (v_root[3] world frame, omega_root[3] body frame, theta_dot[nh])
+ *                                                          nv = nb + 5
+ *   cpg = (x_1, y_1, x_2, y_2, ...)                        2 nh entries
+ * Host state arrays use fixed row strides SIM_QW, SIM_VW, SIM_SW floats per
+ * variant; unused tail entries are ignored on input and zero on output.
+ *
+ * Ownership.  All device memory is owned by the context.  Every host
+ * pointer is owned by the caller and only read (or written) during the
+ * call.  Nothing crosses the ABI as an exception; every entry point returns
+ * a sim_status, and sim_last_error() explains the last failure.
+ * Threading: one context per host thread; a context is not re-entrant.
+ * Stream: work is enqueued on the context's stream (sim_config.stream, a
+ * cudaStream_t cast to uint64_t, or 0 for a stream the context creates).
+ */
+#ifndef B3SIM_H
+#define B3SIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim_ctx sim_ctx_t;   /* opaque context                       */
+
+#define SIM_MAX_BODIES 26   /* core + up to 25 hinged bricks              */
+#define SIM_QW 32           /* host row stride of q                        */
+#define SIM_VW 32           /* host row stride of v                        */
+#define SIM_SW 64           /* host row stride of the CPG state            */
+#define SIM_MAX_CONTACT_CAP 64
+#define SIM_MAX_CANDIDATES 256
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = -1,   /* bad argument: null pointer, size or range       */
+    SIM_ECUDA = -2,    /* a CUDA call failed                              */
+    SIM_ENOMEM = -3,   /* device or host allocation failed                */
+    SIM_ESTATE = -4    /* call out of order (e.g. step before population) */
+} sim_status;
+
+/* per-variant status bits, returned by sim_read_state */
+#define SIM_ST_NONFINITE 1u        /* state became non-finite: frozen      */
+#define SIM_ST_OVERFLOW 2u         /* more contacts than contact_cap       */
+#define SIM_ST_CHOL 4u             /* non-positive Cholesky pivot: frozen  */
+#define SIM_ST_CANDIDATES 8u       /* more than SIM_MAX_CANDIDATES contact
+                                      candidates; the extra were dropped    */
+
+typedef struct {
+    double dt;                /* step [s]                                    */
+    float gravity[3];         /* [m/s^2], z up                               */
+    int32_t pgs_iters;        /* Gauss-Seidel sweeps per step (>= 1)         */
+    float soft_tau;           /* contact time constant [s]                   */
+    float soft_zeta;          /* contact damping ratio                       */
+    float mu;                 /* friction coefficient                        */
+    int32_t contact_cap;      /* 1..SIM_MAX_CONTACT_CAP                      */
+    float kp, kd, tau_max;    /* PD servo gains and torque limit             */
+    float theta_max;          /* CPG amplitude [rad]                         */
+    float armature;           /* rotor inertia added on hinge diagonals      */
+    int32_t ground;           /* 1: box/plane contacts                       */
+    int32_t box_box;          /* 1: box/box contacts inside a robot          */
+    int32_t actuate;          /* 1: CPG + PD torques                         */
+    int32_t device;           /* CUDA device ordinal                         */
+    uint64_t stream;          /* cudaStream_t or 0                           */
+    int32_t steps_per_launch; /* persistent chunk; 0: library default        */
+    int32_t warps_per_block;  /* 0: autotuned default                        */
+} sim_config;
+
+/* Model of one variant.  Arrays have n_bodies entries (per body) unless
+ * stated; body 0 is the core (free root), parent[b] < b for b >= 1. */
+typedef struct {
+    int32_t n_bodies;             /* 1..SIM_MAX_BODIES                        */
+    const int8_t* parent;         /* parent body, -1 for body 0               */
+    const int8_t* hinge_axis;     /* hinge axis index 0..2 in the body frame  */
+    const uint32_t* exclude;      /* bit j: body never collides with body j   */
+    const float* joint_frame;     /* 12 per body: R (3x3 row-major), p (3):
+                                     body frame at zero angle in its parent  */
+    const float* half_size;       /* 3 per body: box half extents [m]         */
+    const float* box_center;      /* 3 per body: box centre in body frame [m] */
+    const float* mass;            /* [kg]; inertia is that of a solid box     */
+    const float* cpg_w_internal;  /* per body: oscillator weight of hinge b   */
+    const float* cpg_w_couple;    /* per body: coupling of hinge b to the
+                                     hinge of its parent (0 if parent = 0)   */
+} sim_variant_desc;
+
+typedef struct {
+    double contacts;          /* sum over variants and steps of contacts     */
+    double narrow_pairs;      /* box/box pairs through the narrow phase      */
+    double broad_pairs;       /* box/box pairs through the broad phase       */
+    double variant_steps;     /* variants x steps advanced                   */
+} sim_counters;
+
+/* Create a context on cfg->device.  Copies cfg.  *out is NULL on failure. */
+int sim_create(const sim_config* cfg, sim_ctx_t** out);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+int sim_destroy(sim_ctx_t* ctx);
+
+/* Replace the population with n variants (n >= 1).  Copies every array.
+ * The state is reset to q = v = 0, cpg = 0 and must be set with
+ * sim_set_state before stepping.  Internally variants are reordered by size;
+ * every other call uses the caller's order. */
+int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n);
+
+/* Set state of variants [first, first+count) from host rows (strides SIM_QW,
+ * SIM_VW, SIM_SW).  cpg may be NULL (kept).  Clears their status bits and
+ * records the current core xy as the fitness origin.  Synchronous. */
+int sim_set_state(sim_ctx_t* ctx, int32_t first, int32_t count, const float* q,
+                  const float* v, const float* cpg);
+
+/* Advance every variant n_steps (>= 0) steps.  Asynchronous on the context
+ * stream (a captured CUDA graph per distinct n_steps); launch errors are
+ * returned, execution errors surface at the next synchronising call. */
+int sim_step_n(sim_ctx_t* ctx, int32_t n_steps);
+
+/* Copy state of variants [first, first+count) to host rows; any output
+ * pointer may be NULL.  status gets the per-variant SIM_ST_* bits.
+ * Synchronises the context stream. */
+int sim_read_state(sim_ctx_t* ctx, int32_t first, int32_t count, float* q, float* v,
+                   float* cpg, uint32_t* status);
+
+/* Core xy displacement of variants [0, n) since their last sim_set_state.
+ * Synchronises the context stream. */
+int sim_fitness(sim_ctx_t* ctx, float* out, int32_t n);
+
+/* Time the candidate launch shapes on probe_steps steps of the current
+ * population (state is saved and restored) and keep the fastest. */
+int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps);
+
+/* Work counters accumulated since sim_set_population (synchronises). */
+int sim_counters_read(sim_ctx_t* ctx, sim_counters* out);
+
+/* Contact list of the last step of variant i (caller's order): up to
+ * max_contacts rows of 8 floats (point relative to the core origin (3),
+ * normal from body b to body a (3), depth, body a) and the body b of each
+ * row (-1: ground) in b_out.  *n_out gets the count.  Synchronises. */
+int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* rows,
+                       int32_t* b_out, int32_t* n_out);
+
+/* Human-readable description of the last failure on this context ("" if
+ * none).  ctx may be NULL for a failure in sim_create. */
+const char* sim_last_error(const sim_ctx_t* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

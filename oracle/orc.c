@@ -48,6 +48,7 @@ typedef struct {
 } work;
 
 #define ORC_PI 3.14159265358979323846
+#define ORC_AMIN 1e-10  /* rows with J M^-1 J^T below this are frozen */
 #define FL(w, n) ((w)->flops[(w)->phase] += (double)(n))
 
 static void note_margin(work* w, double m) {
@@ -558,8 +559,10 @@ static void box_box(work* w, const orc_model* m, int ia, int ib) {
             for (int v = 0; v < np; ++v) {
                 int nx = (v + 1) % np;
                 int in_v = dist[v] <= 0.0, in_n = dist[nx] <= 0.0;
-                if (in_v) { memcpy(tmp[no], poly[v], sizeof tmp[0]); ++no; }
-                if (in_v != in_n) {
+                /* a convex quad gains at most one vertex per plane (<= 8); rounding
+                   can only add spurious crossings, which are dropped past 8 */
+                if (in_v && no < 8) { memcpy(tmp[no], poly[v], sizeof tmp[0]); ++no; }
+                if (in_v != in_n && no < 8) {
                     double t = dist[v] / (dist[v] - dist[nx]);
                     for (int k = 0; k < 3; ++k) tmp[no][k] = poly[v][k] + t * (poly[nx][k] - poly[v][k]);
                     FL(w, 2 + 9);
@@ -833,7 +836,10 @@ static int step(work* w, const orc_model* m, const orc_params* prm, double* q, d
             double a = 0.0;
             for (int i = 0; i < nv; ++i) a += w->J[r][i] * w->Wm[r][i];
             FL(w, 2 * nv);
-            w->A[r] = a;
+            /* a row that no dof can move (J = 0, e.g. a tangent normal to the
+               plane of a planar mechanism) carries no impulse: frozen at 0 */
+            note_margin(w, (a - ORC_AMIN) * 1e4);
+            w->A[r] = a > ORC_AMIN ? a : 0.0;
             w->Rs[r] = kappa * a;
             w->tgt[r] = d == 0 ? erp * w->con.depth[k] / dt : 0.0;
             FL(w, d == 0 ? 3 : 1);
@@ -851,7 +857,7 @@ static int step(work* w, const orc_model* m, const orc_params* prm, double* q, d
             double jv = 0.0;
             for (int i = 0; i < nv; ++i) jv += w->J[rn][i] * vv[i];
             double g = jv - w->tgt[rn] + w->Rs[rn] * w->lam[rn];
-            double ln = w->lam[rn] - g / (w->A[rn] + w->Rs[rn]);
+            double ln = w->A[rn] > 0.0 ? w->lam[rn] - g / (w->A[rn] + w->Rs[rn]) : w->lam[rn];
             if (ln < 0.0) ln = 0.0;
             double dn = ln - w->lam[rn];
             for (int i = 0; i < nv; ++i) vv[i] += w->Wm[rn][i] * dn;
@@ -859,8 +865,8 @@ static int step(work* w, const orc_model* m, const orc_params* prm, double* q, d
             FL(w, 4 * nv + 3 + 3 + 1 + 1);
             double j1 = 0.0, j2 = 0.0;
             for (int i = 0; i < nv; ++i) { j1 += w->J[r1][i] * vv[i]; j2 += w->J[r2][i] * vv[i]; }
-            double l1 = w->lam[r1] - (j1 + w->Rs[r1] * w->lam[r1]) / (w->A[r1] + w->Rs[r1]);
-            double l2 = w->lam[r2] - (j2 + w->Rs[r2] * w->lam[r2]) / (w->A[r2] + w->Rs[r2]);
+            double l1 = w->A[r1] > 0.0 ? w->lam[r1] - (j1 + w->Rs[r1] * w->lam[r1]) / (w->A[r1] + w->Rs[r1]) : w->lam[r1];
+            double l2 = w->A[r2] > 0.0 ? w->lam[r2] - (j2 + w->Rs[r2] * w->lam[r2]) / (w->A[r2] + w->Rs[r2]) : w->lam[r2];
             double lim = prm->mu * ln;
             double nt2 = l1 * l1 + l2 * l2;
             FL(w, 4 * nv + 10 + 1 + 3);

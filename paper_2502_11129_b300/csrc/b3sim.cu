@@ -1,0 +1,602 @@
+// b3sim.cu -- host runtime and C ABI of the population simulator.
+//
+// The library owns every device buffer.  A population is packed once into a
+// structure-of-arrays model (per variant: [field][32 body slots]), sorted by
+// robot size so that the warps of a launch carry similar work and the largest
+// robots start first.  Steps run as persistent launches of step_kernel (one
+// warp per robot, many steps per launch); the launch sequence for a given
+// step count is captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "b3sim.h"
+#include "step_kernel.cuh"
+
+using b3::Counters;
+using b3::StepParams;
+
+struct sim_ctx {
+  sim_config cfg{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n = 0;
+  std::vector<int> perm;  // packed index -> caller index
+  std::vector<int> inv;   // caller index -> packed index
+  float* d_mf = nullptr;
+  int* d_mi = nullptr;
+  int4* d_meta = nullptr;
+  uint16_t* d_pairs = nullptr;
+  int* d_perm = nullptr;
+  float* d_q = nullptr;
+  float* d_v = nullptr;
+  float* d_s = nullptr;
+  float* d_fit0 = nullptr;
+  unsigned* d_status = nullptr;
+  Counters* d_counters = nullptr;
+  float* d_scratch = nullptr;
+  int* d_lastnc = nullptr;
+  float* d_stage = nullptr;  // caller-order staging: q | v | s rows
+  unsigned* d_stage_st = nullptr;
+  StepParams P{};
+  int steps_per_launch = 500;
+  int wpb = 4;
+  std::map<long long, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+const char* g_create_error = "";
+std::string g_create_error_buf;
+
+int fail(sim_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(sim_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_population(sim_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+  dfree(ctx->d_mf);
+  dfree(ctx->d_mi);
+  dfree(ctx->d_meta);
+  dfree(ctx->d_pairs);
+  dfree(ctx->d_perm);
+  dfree(ctx->d_q);
+  dfree(ctx->d_v);
+  dfree(ctx->d_s);
+  dfree(ctx->d_fit0);
+  dfree(ctx->d_status);
+  dfree(ctx->d_counters);
+  dfree(ctx->d_scratch);
+  dfree(ctx->d_lastnc);
+  dfree(ctx->d_stage);
+  dfree(ctx->d_stage_st);
+  ctx->n = 0;
+  ctx->perm.clear();
+  ctx->inv.clear();
+}
+
+// caller rows -> packed rows (+ fitness origin, status reset)
+__global__ void scatter_state(const float* __restrict__ sq, const float* __restrict__ sv,
+                              const float* __restrict__ ss, const int* __restrict__ inv_first, int first,
+                              int count, int with_cpg, float* q, float* v, float* s, float* fit0,
+                              unsigned* status) {
+  int i = blockIdx.x;
+  if (i >= count) return;
+  int d = inv_first[first + i];
+  int t = threadIdx.x;
+  if (t < SIM_QW) q[(size_t)d * 32 + t] = sq[(size_t)i * SIM_QW + t];
+  if (t < SIM_VW) v[(size_t)d * 32 + t] = sv[(size_t)i * SIM_VW + t];
+  if (with_cpg && t < SIM_SW) s[(size_t)d * 64 + t] = ss[(size_t)i * SIM_SW + t];
+  if (t == 0) {
+    fit0[2 * d] = sq[(size_t)i * SIM_QW];
+    fit0[2 * d + 1] = sq[(size_t)i * SIM_QW + 1];
+    status[d] = 0u;
+  }
+}
+
+// packed rows -> caller rows
+__global__ void gather_state(const float* __restrict__ q, const float* __restrict__ v, const float* __restrict__ s,
+                             const unsigned* __restrict__ status, const int* __restrict__ inv_first, int first,
+                             int count, float* dq, float* dv, float* ds, unsigned* dst) {
+  int i = blockIdx.x;
+  if (i >= count) return;
+  int d = inv_first[first + i];
+  int t = threadIdx.x;
+  if (t < SIM_QW) dq[(size_t)i * SIM_QW + t] = q[(size_t)d * 32 + t];
+  if (t < SIM_VW) dv[(size_t)i * SIM_VW + t] = v[(size_t)d * 32 + t];
+  if (t < SIM_SW) ds[(size_t)i * SIM_SW + t] = s[(size_t)d * 64 + t];
+  if (t == 0) dst[i] = status[d];
+}
+
+__global__ void fitness_kernel(const float* __restrict__ q, const float* __restrict__ fit0,
+                               const int* __restrict__ inv, int n, float* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int d = inv[i];
+  float dx = q[(size_t)d * 32] - fit0[2 * d];
+  float dy = q[(size_t)d * 32 + 1] - fit0[2 * d + 1];
+  out[i] = sqrtf(dx * dx + dy * dy);
+}
+
+size_t smem_bytes(int wpb) { return (size_t)wpb * sizeof(b3::WarpSmem); }
+
+template <int WPB>
+cudaError_t launch_wpb(sim_ctx* ctx, int nsteps) {
+  const size_t sm = smem_bytes(WPB);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(b3::step_kernel<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  dim3 grid((ctx->n + WPB - 1) / WPB), block(32 * WPB);
+  b3::step_kernel<WPB><<<grid, block, sm, ctx->stream>>>(ctx->d_mf, ctx->d_mi, ctx->d_meta, ctx->d_pairs, ctx->d_q,
+                                                        ctx->d_v, ctx->d_s, ctx->d_status, ctx->d_counters,
+                                                        ctx->d_scratch, ctx->d_lastnc, ctx->n, nsteps, ctx->P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk(sim_ctx* ctx, int nsteps, int wpb) {
+  switch (wpb) {
+    case 1: return launch_wpb<1>(ctx, nsteps);
+    case 2: return launch_wpb<2>(ctx, nsteps);
+    case 4: return launch_wpb<4>(ctx, nsteps);
+    case 8: return launch_wpb<8>(ctx, nsteps);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, int spl) {
+  for (int done = 0; done < n_steps; done += spl) {
+    cudaError_t e = launch_chunk(ctx, std::min(spl, n_steps - done), wpb);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool finite_all(const float* p, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_create(const sim_config* cfg, sim_ctx_t** out) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (!cfg) {
+    g_create_error = "sim_create: cfg is NULL";
+    return SIM_EINVAL;
+  }
+  if (!(cfg->dt > 0.0) || cfg->pgs_iters < 1 || cfg->contact_cap < 1 || cfg->contact_cap > SIM_MAX_CONTACT_CAP ||
+      !(cfg->soft_tau > 0.f) || !(cfg->soft_zeta >= 0.f) || !(cfg->mu >= 0.f) || cfg->steps_per_launch < 0 ||
+      !(cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
+        cfg->warps_per_block == 4 || cfg->warps_per_block == 8)) {
+    g_create_error = "sim_create: configuration out of range";
+    return SIM_EINVAL;
+  }
+  sim_ctx* ctx = new (std::nothrow) sim_ctx();
+  if (!ctx) return SIM_ENOMEM;
+  ctx->cfg = *cfg;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    g_create_error_buf = std::string("sim_create: cudaSetDevice: ") + cudaGetErrorString(e);
+    g_create_error = g_create_error_buf.c_str();
+    delete ctx;
+    return SIM_ECUDA;
+  }
+  if (cfg->stream) {
+    ctx->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_create_error_buf = std::string("sim_create: cudaStreamCreate: ") + cudaGetErrorString(e);
+      g_create_error = g_create_error_buf.c_str();
+      delete ctx;
+      return SIM_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  StepParams& P = ctx->P;
+  const double dt = cfg->dt;
+  const double omg = 2.0 * 3.14159265358979323846 / (double)cfg->soft_tau;
+  const double kden = dt * omg * omg + 2.0 * (double)cfg->soft_zeta * omg;
+  P.dt = (float)dt;
+  P.gx = cfg->gravity[0];
+  P.gy = cfg->gravity[1];
+  P.gz = cfg->gravity[2];
+  P.iters = cfg->pgs_iters;
+  P.mu = cfg->mu;
+  P.erp = (float)(dt * omg * omg / kden);
+  P.kappa = (float)(1.0 / (dt * kden));
+  P.cap = cfg->contact_cap;
+  P.kp = cfg->kp;
+  P.kd = cfg->kd;
+  P.tau_max = cfg->tau_max;
+  P.theta_max = cfg->theta_max;
+  P.armature = cfg->armature;
+  P.ground = cfg->ground ? 1 : 0;
+  P.box_box = cfg->box_box ? 1 : 0;
+  P.actuate = cfg->actuate ? 1 : 0;
+  if (cfg->steps_per_launch > 0) ctx->steps_per_launch = cfg->steps_per_launch;
+  if (cfg->warps_per_block > 0) ctx->wpb = cfg->warps_per_block;
+  *out = ctx;
+  return SIM_OK;
+}
+
+int sim_destroy(sim_ctx_t* ctx) {
+  if (!ctx) return SIM_OK;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_population(ctx);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return SIM_OK;
+}
+
+int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
+  if (!ctx) return SIM_EINVAL;
+  if (!v || n < 1) return fail(ctx, SIM_EINVAL, "sim_set_population: need n >= 1 variants");
+  CK(cudaSetDevice(ctx->cfg.device));
+  // validate
+  for (int i = 0; i < n; ++i) {
+    const sim_variant_desc& d = v[i];
+    const int nb = d.n_bodies;
+    char buf[160];
+    if (nb < 1 || nb > SIM_MAX_BODIES) {
+      snprintf(buf, sizeof buf, "sim_set_population: variant %d has %d bodies (1..%d)", i, nb, SIM_MAX_BODIES);
+      return fail(ctx, SIM_EINVAL, buf);
+    }
+    if (!d.parent || !d.hinge_axis || !d.joint_frame || !d.half_size || !d.box_center || !d.mass) {
+      snprintf(buf, sizeof buf, "sim_set_population: variant %d has a NULL model array", i);
+      return fail(ctx, SIM_EINVAL, buf);
+    }
+    if (d.parent[0] != -1) {
+      snprintf(buf, sizeof buf, "sim_set_population: variant %d: parent[0] must be -1", i);
+      return fail(ctx, SIM_EINVAL, buf);
+    }
+    for (int b = 0; b < nb; ++b) {
+      if ((b > 0 && (d.parent[b] < 0 || d.parent[b] >= b)) || d.hinge_axis[b] < 0 || d.hinge_axis[b] > 2 ||
+          !(d.mass[b] > 0.f) || !finite_all(d.joint_frame + 12 * b, 12) || !finite_all(d.half_size + 3 * b, 3) ||
+          !finite_all(d.box_center + 3 * b, 3) || !(d.half_size[3 * b] > 0.f) || !(d.half_size[3 * b + 1] > 0.f) ||
+          !(d.half_size[3 * b + 2] > 0.f) ||
+          (d.cpg_w_internal && !std::isfinite(d.cpg_w_internal[b])) ||
+          (d.cpg_w_couple && !std::isfinite(d.cpg_w_couple[b]))) {
+        snprintf(buf, sizeof buf, "sim_set_population: variant %d body %d is invalid", i, b);
+        return fail(ctx, SIM_EINVAL, buf);
+      }
+    }
+  }
+  free_population(ctx);
+  // pack in size order (largest first, stable)
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return v[a].n_bodies > v[b].n_bodies; });
+  std::vector<int> inv(n);
+  for (int k = 0; k < n; ++k) inv[perm[k]] = k;
+  std::vector<float> mf((size_t)n * b3::NF * 32, 0.f);
+  std::vector<int> mi((size_t)n * b3::NI * 32, 0);
+  std::vector<int4> meta(n);
+  std::vector<uint16_t> pairs;
+  for (int k = 0; k < n; ++k) {
+    const sim_variant_desc& d = v[perm[k]];
+    const int nb = d.n_bodies;
+    float* F = mf.data() + (size_t)k * b3::NF * 32;
+    int* I = mi.data() + (size_t)k * b3::NI * 32;
+    int depth[32] = {0};
+    unsigned path[32] = {0}, child[32] = {0};
+    int maxdepth = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int p = b == 0 ? -1 : d.parent[b];
+      depth[b] = p < 0 ? 0 : depth[p] + 1;
+      path[b] = (p < 0 ? 0u : path[p]) | (1u << b);
+      if (p >= 0) child[p] |= 1u << b;
+      maxdepth = std::max(maxdepth, depth[b]);
+    }
+    for (int b = 0; b < 32; ++b) {
+      I[b3::I_PARENT * 32 + b] = b < nb ? (b == 0 ? -1 : d.parent[b]) : -1;
+      I[b3::I_AXIS * 32 + b] = b < nb ? d.hinge_axis[b] : 0;
+      I[b3::I_PATH * 32 + b] = (int)(b < nb ? path[b] : 0u);
+      I[b3::I_CHILD * 32 + b] = (int)(b < nb ? child[b] : 0u);
+      I[b3::I_DEPTH * 32 + b] = b < nb ? depth[b] : 0;
+      if (b >= nb) {
+        F[(b3::F_RFIX + 0) * 32 + b] = 1.f;
+        F[(b3::F_RFIX + 4) * 32 + b] = 1.f;
+        F[(b3::F_RFIX + 8) * 32 + b] = 1.f;
+        continue;
+      }
+      for (int t = 0; t < 9; ++t) F[(b3::F_RFIX + t) * 32 + b] = d.joint_frame[12 * b + t];
+      for (int t = 0; t < 3; ++t) {
+        F[(b3::F_PFIX + t) * 32 + b] = d.joint_frame[12 * b + 9 + t];
+        F[(b3::F_HALF + t) * 32 + b] = d.half_size[3 * b + t];
+        F[(b3::F_COM + t) * 32 + b] = d.box_center[3 * b + t];
+      }
+      const double m = d.mass[b];
+      const double hx = d.half_size[3 * b], hy = d.half_size[3 * b + 1], hz = d.half_size[3 * b + 2];
+      F[b3::F_MASS * 32 + b] = d.mass[b];
+      F[(b3::F_ID + 0) * 32 + b] = (float)(m * (hy * hy + hz * hz) / 3.0);
+      F[(b3::F_ID + 1) * 32 + b] = (float)(m * (hx * hx + hz * hz) / 3.0);
+      F[(b3::F_ID + 2) * 32 + b] = (float)(m * (hx * hx + hy * hy) / 3.0);
+      F[b3::F_WINT * 32 + b] = d.cpg_w_internal ? d.cpg_w_internal[b] : 0.f;
+      F[b3::F_WCPL * 32 + b] = d.cpg_w_couple ? d.cpg_w_couple[b] : 0.f;
+      F[b3::F_RAD * 32 + b] = (float)std::sqrt(hx * hx + hy * hy + hz * hz);
+    }
+    const int off = (int)pairs.size();
+    for (int a = 0; a < nb; ++a)
+      for (int b = a + 1; b < nb; ++b) {
+        if (d.parent[b] == a) continue;
+        if (d.exclude && (((d.exclude[a] >> b) & 1u) || ((d.exclude[b] >> a) & 1u))) continue;
+        pairs.push_back((uint16_t)((a << 8) | b));
+      }
+    meta[k] = make_int4(nb, maxdepth, (int)pairs.size() - off, off);
+  }
+  if (pairs.empty()) pairs.push_back(0);
+  ctx->n = n;
+  ctx->perm = perm;
+  ctx->inv = inv;
+  const size_t N = (size_t)n;
+  cudaError_t e;
+#define ALLOC(ptr, bytes)                                         \
+  e = cudaMalloc(&(ptr), (bytes));                                \
+  if (e != cudaSuccess) {                                         \
+    free_population(ctx);                                         \
+    return fail(ctx, SIM_ENOMEM, std::string("cudaMalloc ") + #ptr); \
+  }
+  ALLOC(ctx->d_mf, mf.size() * sizeof(float));
+  ALLOC(ctx->d_mi, mi.size() * sizeof(int));
+  ALLOC(ctx->d_meta, N * sizeof(int4));
+  ALLOC(ctx->d_pairs, pairs.size() * sizeof(uint16_t));
+  ALLOC(ctx->d_perm, N * sizeof(int));
+  ALLOC(ctx->d_q, N * 32 * sizeof(float));
+  ALLOC(ctx->d_v, N * 32 * sizeof(float));
+  ALLOC(ctx->d_s, N * 64 * sizeof(float));
+  ALLOC(ctx->d_fit0, N * 2 * sizeof(float));
+  ALLOC(ctx->d_status, N * sizeof(unsigned));
+  ALLOC(ctx->d_counters, N * sizeof(Counters));
+  ALLOC(ctx->d_scratch, N * b3::kScratchFloats * sizeof(float));
+  ALLOC(ctx->d_lastnc, N * sizeof(int));
+  ALLOC(ctx->d_stage, N * (SIM_QW + SIM_VW + SIM_SW) * sizeof(float));
+  ALLOC(ctx->d_stage_st, N * sizeof(unsigned));
+#undef ALLOC
+  CK(cudaMemcpyAsync(ctx->d_mf, mf.data(), mf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_mi, mi.data(), mi.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_meta, meta.data(), N * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_pairs, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_perm, ctx->inv.data(), N * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_q, 0, N * 32 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_v, 0, N * 32 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_s, 0, N * 64 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_fit0, 0, N * 2 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_status, 0, N * sizeof(unsigned), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_counters, 0, N * sizeof(Counters), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_lastnc, 0, N * sizeof(int), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SIM_OK;
+}
+
+int sim_set_state(sim_ctx_t* ctx, int32_t first, int32_t count, const float* q, const float* v, const float* cpg) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_set_state: no population");
+  if (!q || !v || first < 0 || count < 0 || first + count > ctx->n)
+    return fail(ctx, SIM_EINVAL, "sim_set_state: bad range or NULL q/v");
+  if (count == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  float* sq = ctx->d_stage;
+  float* sv = sq + (size_t)count * SIM_QW;
+  float* ss = sv + (size_t)count * SIM_VW;
+  CK(cudaMemcpyAsync(sq, q, (size_t)count * SIM_QW * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(sv, v, (size_t)count * SIM_VW * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  if (cpg)
+    CK(cudaMemcpyAsync(ss, cpg, (size_t)count * SIM_SW * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  scatter_state<<<count, 64, 0, ctx->stream>>>(sq, sv, ss, ctx->d_perm, first, count, cpg ? 1 : 0, ctx->d_q,
+                                               ctx->d_v, ctx->d_s, ctx->d_fit0, ctx->d_status);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SIM_OK;
+}
+
+int sim_step_n(sim_ctx_t* ctx, int32_t n_steps) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_step_n: no population");
+  if (n_steps < 0) return fail(ctx, SIM_EINVAL, "sim_step_n: n_steps < 0");
+  if (n_steps == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  const long long key = ((long long)n_steps << 8) | ctx->wpb;
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = enqueue_steps(ctx, n_steps, ctx->wpb, ctx->steps_per_launch);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (le != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(ctx, le, "sim_step_n: launch");
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "sim_step_n: capture");
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "sim_step_n: instantiate");
+    it = ctx->graphs.emplace(key, ge).first;
+  }
+  CK(cudaGraphLaunch(it->second, ctx->stream));
+  return SIM_OK;
+}
+
+int sim_read_state(sim_ctx_t* ctx, int32_t first, int32_t count, float* q, float* v, float* cpg, uint32_t* status) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_read_state: no population");
+  if (first < 0 || count < 0 || first + count > ctx->n) return fail(ctx, SIM_EINVAL, "sim_read_state: bad range");
+  if (count == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  float* dq = ctx->d_stage;
+  float* dv = dq + (size_t)count * SIM_QW;
+  float* ds = dv + (size_t)count * SIM_VW;
+  gather_state<<<count, 64, 0, ctx->stream>>>(ctx->d_q, ctx->d_v, ctx->d_s, ctx->d_status, ctx->d_perm, first,
+                                              count, dq, dv, ds, ctx->d_stage_st);
+  CK(cudaGetLastError());
+  if (q) CK(cudaMemcpyAsync(q, dq, (size_t)count * SIM_QW * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  if (v) CK(cudaMemcpyAsync(v, dv, (size_t)count * SIM_VW * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  if (cpg)
+    CK(cudaMemcpyAsync(cpg, ds, (size_t)count * SIM_SW * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  if (status)
+    CK(cudaMemcpyAsync(status, ctx->d_stage_st, (size_t)count * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SIM_OK;
+}
+
+int sim_fitness(sim_ctx_t* ctx, float* out, int32_t n) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_fitness: no population");
+  if (!out || n < 0 || n > ctx->n) return fail(ctx, SIM_EINVAL, "sim_fitness: bad n or NULL out");
+  if (n == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  float* d_out = ctx->d_stage;
+  fitness_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_q, ctx->d_fit0, ctx->d_perm, n, d_out);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SIM_OK;
+}
+
+int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_autotune: no population");
+  if (probe_steps < 1) return fail(ctx, SIM_EINVAL, "sim_autotune: probe_steps < 1");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const size_t N = (size_t)ctx->n;
+  // save state and counters
+  std::vector<float> q(N * 32), v(N * 32), s(N * 64);
+  std::vector<unsigned> st(N);
+  std::vector<Counters> cn(N);
+  CK(cudaMemcpyAsync(q.data(), ctx->d_q, q.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(v.data(), ctx->d_v, v.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(s.data(), ctx->d_s, s.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(st.data(), ctx->d_status, N * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(cn.data(), ctx->d_counters, N * sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  auto restore = [&]() -> cudaError_t {
+    cudaMemcpyAsync(ctx->d_q, q.data(), q.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_v, v.data(), v.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_s, s.data(), s.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_status, st.data(), N * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(ctx->d_counters, cn.data(), N * sizeof(Counters), cudaMemcpyHostToDevice, ctx->stream);
+    return cudaStreamSynchronize(ctx->stream);
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cands[4] = {1, 2, 4, 8};
+  float best_ms = 1e30f;
+  int best = ctx->wpb;
+  for (int c : cands) {
+    cudaError_t e = restore();
+    if (e != cudaSuccess) break;
+    e = enqueue_steps(ctx, probe_steps, c, probe_steps);  // warm-up (and attribute set-up)
+    if (e != cudaSuccess) continue;
+    restore();
+    cudaEventRecord(e0, ctx->stream);
+    e = enqueue_steps(ctx, probe_steps, c, probe_steps);
+    cudaEventRecord(e1, ctx->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || e != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(restore());
+  ctx->wpb = best;
+  return SIM_OK;
+}
+
+int sim_counters_read(sim_ctx_t* ctx, sim_counters* out) {
+  if (!ctx || !out) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_counters_read: no population");
+  CK(cudaSetDevice(ctx->cfg.device));
+  std::vector<Counters> cn(ctx->n);
+  CK(cudaMemcpyAsync(cn.data(), ctx->d_counters, cn.size() * sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  sim_counters r{};
+  for (const Counters& c : cn) {
+    r.contacts += (double)c.contacts;
+    r.narrow_pairs += (double)c.narrow;
+    r.broad_pairs += (double)c.broad;
+    r.variant_steps += (double)c.steps;
+  }
+  *out = r;
+  return SIM_OK;
+}
+
+int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* rows, int32_t* b_out,
+                       int32_t* n_out) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_debug_contacts: no population");
+  if (i < 0 || i >= ctx->n || max_contacts < 0 || !n_out || (max_contacts > 0 && (!rows || !b_out)))
+    return fail(ctx, SIM_EINVAL, "sim_debug_contacts: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const int d = ctx->inv[i];
+  int nc = 0;
+  CK(cudaMemcpyAsync(&nc, ctx->d_lastnc + d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int m = std::min(nc, (int)max_contacts);
+  std::vector<float> buf((size_t)std::max(m, 1) * b3::kCandW);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(buf.data(), ctx->d_scratch + (size_t)d * b3::kScratchFloats, (size_t)m * b3::kCandW * 4,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  for (int k = 0; k < m; ++k) {
+    const float* r = buf.data() + (size_t)k * b3::kCandW;
+    int ab;
+    std::memcpy(&ab, r + 7, 4);
+    for (int t = 0; t < 7; ++t) rows[8 * k + t] = r[t];
+    rows[8 * k + 7] = (float)(ab & 0xff);
+    const int b = (ab >> 8) & 0xff;
+    b_out[k] = b == 255 ? -1 : b;
+  }
+  *n_out = nc;
+  return SIM_OK;
+}
+
+const char* sim_last_error(const sim_ctx_t* ctx) {
+  if (!ctx) return g_create_error;
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+"""Python binding of the C ABI in include/b3sim.h (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library ``libb3sim.so``; this
+module only converts numpy arrays to the ABI's structs and pointers.  There
+is no CPU fallback: if the library is missing or no CUDA device is present,
+construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import population as popmod
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libb3sim.so")
+
+SIM_MAX_BODIES = 26
+SIM_QW, SIM_VW, SIM_SW = 32, 32, 64
+SIM_MAX_CONTACT_CAP = 64
+ST_NONFINITE, ST_OVERFLOW, ST_CHOL, ST_CANDIDATES = 1, 2, 4, 8
+STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: "SIM_ESTATE"}
+
+EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
+           "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
+           "sim_debug_contacts", "sim_last_error"]
+
+
+class SimConfig(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double), ("gravity", C.c_float * 3), ("pgs_iters", C.c_int32),
+        ("soft_tau", C.c_float), ("soft_zeta", C.c_float), ("mu", C.c_float),
+        ("contact_cap", C.c_int32), ("kp", C.c_float), ("kd", C.c_float),
+        ("tau_max", C.c_float), ("theta_max", C.c_float), ("armature", C.c_float),
+        ("ground", C.c_int32), ("box_box", C.c_int32), ("actuate", C.c_int32),
+        ("device", C.c_int32), ("stream", C.c_uint64), ("steps_per_launch", C.c_int32),
+        ("warps_per_block", C.c_int32),
+    ]
+
+
+class VariantDesc(C.Structure):
+    _fields_ = [
+        ("n_bodies", C.c_int32), ("parent", C.POINTER(C.c_int8)), ("hinge_axis", C.POINTER(C.c_int8)),
+        ("exclude", C.POINTER(C.c_uint32)), ("joint_frame", C.POINTER(C.c_float)),
+        ("half_size", C.POINTER(C.c_float)), ("box_center", C.POINTER(C.c_float)),
+        ("mass", C.POINTER(C.c_float)), ("cpg_w_internal", C.POINTER(C.c_float)),
+        ("cpg_w_couple", C.POINTER(C.c_float)),
+    ]
+
+
+class Counters(C.Structure):
+    _fields_ = [("contacts", C.c_double), ("narrow_pairs", C.c_double),
+                ("broad_pairs", C.c_double), ("variant_steps", C.c_double)]
+
+
+DEFAULTS = dict(dt=0.002, gravity=(0.0, 0.0, -9.81), pgs_iters=30, soft_tau=0.02, soft_zeta=1.0,
+                mu=1.0, contact_cap=64, kp=2.0, kd=0.05, tau_max=1.0, theta_max=np.pi / 2,
+                armature=1e-4, ground=1, box_box=1, actuate=1, device=0, stream=0,
+                steps_per_launch=0, warps_per_block=0)
+
+_lib = None
+
+
+class SimError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libb3sim.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise SimError(f"{LIB_PATH} is missing; build it with python -m paper_2502_11129_b300.build")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        vp = C.c_void_p
+        L.sim_create.argtypes = [P(SimConfig), P(vp)]
+        L.sim_destroy.argtypes = [vp]
+        L.sim_set_population.argtypes = [vp, P(VariantDesc), C.c_int32]
+        L.sim_set_state.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.sim_step_n.argtypes = [vp, C.c_int32]
+        L.sim_read_state.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp]
+        L.sim_fitness.argtypes = [vp, vp, C.c_int32]
+        L.sim_autotune.argtypes = [vp, C.c_int32]
+        L.sim_counters_read.argtypes = [vp, P(Counters)]
+        L.sim_debug_contacts.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, P(C.c_int32)]
+        L.sim_last_error.argtypes = [vp]
+        L.sim_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class Population32:
+    """float32 / int8 host copies of a Population laid out for the ABI."""
+
+    def __init__(self, pop: popmod.Population):
+        n = pop.n
+        self.n = n
+        self.parent = np.ascontiguousarray(pop.parent, dtype=np.int8)
+        self.axis = np.ascontiguousarray(pop.axis, dtype=np.int8)
+        self.exclude = np.ascontiguousarray(pop.exclude, dtype=np.uint32)
+        jf = np.concatenate([pop.R_fix, pop.p_fix], axis=2)
+        self.joint_frame = np.ascontiguousarray(jf, dtype=np.float32)
+        self.half = np.ascontiguousarray(pop.half, dtype=np.float32)
+        self.com = np.ascontiguousarray(pop.com, dtype=np.float32)
+        self.mass = np.ascontiguousarray(pop.mass, dtype=np.float32)
+        self.w_int = np.ascontiguousarray(pop.w_int, dtype=np.float32)
+        self.w_cpl = np.ascontiguousarray(pop.w_cpl, dtype=np.float32)
+        self.descs = (VariantDesc * n)()
+        f = C.POINTER(C.c_float)
+        for i in range(n):
+            d = self.descs[i]
+            d.n_bodies = int(pop.nb[i])
+            d.parent = self.parent[i].ctypes.data_as(C.POINTER(C.c_int8))
+            d.hinge_axis = self.axis[i].ctypes.data_as(C.POINTER(C.c_int8))
+            d.exclude = self.exclude[i].ctypes.data_as(C.POINTER(C.c_uint32))
+            d.joint_frame = self.joint_frame[i].ctypes.data_as(f)
+            d.half_size = self.half[i].ctypes.data_as(f)
+            d.box_center = self.com[i].ctypes.data_as(f)
+            d.mass = self.mass[i].ctypes.data_as(f)
+            d.cpg_w_internal = self.w_int[i].ctypes.data_as(f)
+            d.cpg_w_couple = self.w_cpl[i].ctypes.data_as(f)
+
+
+def state_rows(pop: popmod.Population, q, v, s):
+    """Host rows with the ABI strides (float32)."""
+    n = pop.n
+    Q = np.zeros((n, SIM_QW), np.float32)
+    V = np.zeros((n, SIM_VW), np.float32)
+    S = np.zeros((n, SIM_SW), np.float32)
+    q = np.asarray(q)
+    v = np.asarray(v)
+    s = np.asarray(s)
+    for i in range(n):
+        nq, nv, ns = int(pop.nb[i]) + 6, int(pop.nb[i]) + 5, 2 * (int(pop.nb[i]) - 1)
+        Q[i, :nq] = q[i, :nq]
+        V[i, :nv] = v[i, :nv]
+        S[i, :ns] = s[i, :ns]
+    return Q, V, S
+
+
+class Sim:
+    """One simulation context on one CUDA device."""
+
+    def __init__(self, **cfg):
+        c = dict(DEFAULTS)
+        c.update(cfg)
+        self.cfg = c
+        sc = SimConfig()
+        for k, val in c.items():
+            if k == "gravity":
+                for i in range(3):
+                    sc.gravity[i] = val[i]
+            else:
+                setattr(sc, k, val)
+        h = C.c_void_p()
+        rc = lib().sim_create(C.byref(sc), C.byref(h))
+        if rc != 0:
+            raise SimError(f"sim_create: {STATUS.get(rc, rc)}: {lib().sim_last_error(None).decode()}")
+        self.h = h
+        self.n = 0
+        self._pop = None
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = lib().sim_last_error(self.h).decode()
+            raise SimError(f"{what}: {STATUS.get(rc, rc)}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_population(self, pop: popmod.Population):
+        p32 = Population32(pop)
+        self._check(lib().sim_set_population(self.h, p32.descs, pop.n), "sim_set_population")
+        self._pop = pop
+        self.n = pop.n
+
+    def set_state(self, Q, V, S=None, first: int = 0):
+        Q = np.ascontiguousarray(Q, np.float32)
+        V = np.ascontiguousarray(V, np.float32)
+        S = None if S is None else np.ascontiguousarray(S, np.float32)
+        count = Q.shape[0]
+        assert Q.shape[1] == SIM_QW and V.shape == (count, SIM_VW)
+        assert S is None or S.shape == (count, SIM_SW)
+        self._check(lib().sim_set_state(self.h, first, count, _ptr(Q), _ptr(V), _ptr(S)), "sim_set_state")
+
+    def set_state_ptr(self, first, count, q_ptr, v_ptr, s_ptr):
+        """Host pointers (e.g. pinned torch tensors) with the ABI strides."""
+        self._check(lib().sim_set_state(self.h, first, count, C.c_void_p(q_ptr), C.c_void_p(v_ptr),
+                                        C.c_void_p(s_ptr) if s_ptr else None), "sim_set_state")
+
+    def step(self, n_steps: int):
+        self._check(lib().sim_step_n(self.h, int(n_steps)), "sim_step_n")
+
+    def read_state(self, first: int = 0, count: int | None = None):
+        count = self.n - first if count is None else count
+        Q = np.zeros((count, SIM_QW), np.float32)
+        V = np.zeros((count, SIM_VW), np.float32)
+        S = np.zeros((count, SIM_SW), np.float32)
+        st = np.zeros(count, np.uint32)
+        self._check(lib().sim_read_state(self.h, first, count, _ptr(Q), _ptr(V), _ptr(S), _ptr(st)),
+                    "sim_read_state")
+        return Q, V, S, st
+
+    def read_state_ptr(self, first, count, q_ptr, v_ptr, s_ptr, st_ptr):
+        self._check(lib().sim_read_state(self.h, first, count, C.c_void_p(q_ptr), C.c_void_p(v_ptr),
+                                         C.c_void_p(s_ptr) if s_ptr else None,
+                                         C.c_void_p(st_ptr) if st_ptr else None), "sim_read_state")
+
+    def fitness(self, n: int | None = None):
+        n = self.n if n is None else n
+        out = np.zeros(n, np.float32)
+        self._check(lib().sim_fitness(self.h, _ptr(out), n), "sim_fitness")
+        return out
+
+    def autotune(self, probe_steps: int = 50):
+        self._check(lib().sim_autotune(self.h, int(probe_steps)), "sim_autotune")
+
+    def counters(self) -> dict:
+        c = Counters()
+        self._check(lib().sim_counters_read(self.h, C.byref(c)), "sim_counters_read")
+        return dict(contacts=c.contacts, narrow_pairs=c.narrow_pairs, broad_pairs=c.broad_pairs,
+                    variant_steps=c.variant_steps)
+
+    def debug_contacts(self, i: int, max_contacts: int = 64):
+        rows = np.zeros((max_contacts, 8), np.float32)
+        bb = np.zeros(max_contacts, np.int32)
+        n = C.c_int32(0)
+        self._check(lib().sim_debug_contacts(self.h, i, max_contacts, _ptr(rows), _ptr(bb), C.byref(n)),
+                    "sim_debug_contacts")
+        m = min(n.value, max_contacts)
+        return dict(n=n.value, p=rows[:m, 0:3], nrm=rows[:m, 3:6], depth=rows[:m, 6],
+                    a=rows[:m, 7].astype(np.int32), b=bb[:m])

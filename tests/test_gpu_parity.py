@@ -1,0 +1,259 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances:
+  * one step from identical FP32-rounded states: per variant
+    |dx| / max(|x_ref|, 1) <= 1e-5 for each of q, v and the CPG state;
+  * contact-free robots (lifted 1 m, 200 steps): core position error
+    <= 1e-4 m;
+  * contact-rich runs (chaotic): population-mean fitness within 2 %.
+Variants whose step contains a discrete decision (contact activation, SAT
+axis, clipping side, overflow cut) within 1e-5 of its threshold in the oracle
+are near-threshold: FP32 and FP64 may legitimately take different branches
+there.  They are counted and reported, and must stay a small minority.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2502_11129_b300 import population as P
+from paper_2502_11129_b300 import sim as S
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-5
+MARGIN = 1e-5
+
+
+def oracle():
+    from oracle import oracle as O
+    return O
+
+
+def ncores():
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+def _gpu_sim(pop, **cfg):
+    sm = S.Sim(**cfg)
+    sm.set_population(pop)
+    return sm
+
+
+def _oracle_params(O, **cfg):
+    keep = {k: v for k, v in cfg.items() if k in ("dt", "gravity", "pgs_iters", "mu", "contact_cap",
+                                                 "ground", "box_box", "actuate", "armature")}
+    return O.default_params(**keep)
+
+
+def _one_step(pop, q, v, s, **cfg):
+    """Returns per-variant relative errors of q, v, s and oracle margins."""
+    O = oracle()
+    pop32 = pop.as_float32()
+    Q, V, Sx = S.state_rows(pop32, q, v, s)
+    sm = _gpu_sim(pop32, **cfg)
+    sm.set_state(Q, V, Sx)
+    sm.step(1)
+    gq, gv, gs, gst = sm.read_state()
+    prm = _oracle_params(O, **cfg)
+    errs = np.zeros((pop.n, 3))
+    margins = np.zeros(pop.n)
+    ost = np.zeros(pop.n, np.uint32)
+    for i in range(pop.n):
+        m = O.model_from_population(pop32, i)
+        nq, nv, ns = O.nq(m), O.nv(m), 2 * (m.nb - 1)
+        s64 = np.zeros(2 * O.MAXB)
+        s64[:ns] = Sx[i, :ns]
+        oq, ov, os_, st, stats = O.run(m, Q[i, :nq].astype(np.float64), V[i, :nv].astype(np.float64), s64, 1, prm=prm)
+        margins[i] = stats.margin
+        ost[i] = st
+        for j, (a, b) in enumerate(((gq[i, :nq], oq[:nq]), (gv[i, :nv], ov[:nv]), (gs[i, :ns], os_[:ns]))):
+            errs[i, j] = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1.0) if len(b) else 0.0
+    return errs, margins, ost, gst, sm
+
+
+def _report(name, errs, margins):
+    near = margins < MARGIN
+    bad = (errs.max(axis=1) > TOL_STEP) & ~near
+    msg = (f"{name}: n={len(errs)} near-threshold={near.sum()} worst(q,v,s)={errs.max(axis=0)} "
+           f"worst-away-from-threshold={errs[~near].max(axis=0) if (~near).any() else None} "
+           f"failing={np.nonzero(bad)[0][:10]}")
+    print(msg)
+    return near, bad, msg
+
+
+def test_one_step_free_boxes():
+    pop = P.boxes(64, seed=1)
+    q = pop.q0.copy()
+    q[:32, 2] = np.random.default_rng(0).uniform(0.03, 0.08, 32)  # half of them in contact
+    errs, margins, ost, gst, _ = _one_step(pop, q, pop.v0, np.zeros((64, 64)))
+    near, bad, msg = _report("boxes", errs, margins)
+    assert not bad.any(), msg
+    assert near.mean() < 0.1, msg
+    assert np.array_equal(ost[~near], gst[~near])
+
+
+def test_one_step_quadrupeds_random_states():
+    pop = P.quadrupeds(128, seed=2)
+    q, v, s = P.random_state(pop, seed=5)
+    q[:, 2] = np.random.default_rng(1).uniform(0.03, 0.09, pop.n)
+    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
+    near, bad, msg = _report("quadrupeds", errs, margins)
+    assert not bad.any(), msg
+    assert near.mean() < 0.1, msg
+
+
+def test_one_step_grammar_random_states():
+    pop = P.grammar(256, seed=3)
+    q, v, s = P.random_state(pop, seed=7)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(2).uniform(-0.04, 0.0, pop.n)
+    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
+    near, bad, msg = _report("grammar", errs, margins)
+    assert not bad.any(), msg
+    # random hinge angles put many lattice-aligned bricks in exact SAT ties
+    assert near.mean() < 0.25, msg
+
+
+def test_one_step_grammar_zero_pose_settled_by_oracle():
+    """States taken from an oracle run (realistic contact sets) at step 300."""
+    O = oracle()
+    pop = P.grammar(96, seed=13).as_float32()
+    q, v, s, st, _ = O.run_population(pop, pop.q0, pop.v0, P.cpg_initial(pop), 300, threads=ncores())
+    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
+    near, bad, msg = _report("grammar-settled", errs, margins)
+    assert not bad.any(), msg
+
+
+def test_contact_lists_match_oracle():
+    """Contact generation (counts, bodies, order bit-exact; geometry to 1e-5)."""
+    O = oracle()
+    pop = P.grammar(64, seed=31).as_float32()
+    q, v, s = P.random_state(pop, seed=9, angle=1.0)
+    q[:, 2] = pop.q0[:, 2] - 0.02
+    Q, V, Sx = S.state_rows(pop, q, v, s)
+    sm = _gpu_sim(pop)
+    sm.set_state(Q, V, Sx)
+    sm.step(1)
+    prm = O.default_params()
+    checked = 0
+    for i in range(pop.n):
+        m = O.model_from_population(pop, i)
+        c = O.contacts(m, Q[i, :O.nq(m)].astype(np.float64), prm)
+        if c["margin"] < MARGIN:
+            continue
+        g = sm.debug_contacts(i)
+        assert g["n"] == len(c["a"]), (i, g["n"], len(c["a"]))
+        assert np.array_equal(g["a"], c["a"]) and np.array_equal(g["b"], c["b"]), i
+        assert np.allclose(g["depth"], c["depth"], atol=1e-5), i
+        assert np.allclose(g["nrm"], c["n"], atol=1e-4), i
+        assert np.allclose(g["p"], c["p"] - Q[i, :3], atol=1e-5), i
+        checked += 1
+    assert checked > pop.n // 2
+
+
+def test_contact_free_trajectories_200_steps():
+    """Lifted 1 m, no box/box: core position within 1e-4 m of the oracle
+    for 200 steps (0.4 s of fall, no ground contact yet)."""
+    O = oracle()
+    for pop in (P.quadrupeds(64, seed=2), P.grammar(128, seed=3)):
+        pop = P.lift(pop, 1.0).as_float32()
+        s0 = P.cpg_initial(pop)
+        Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+        sm = _gpu_sim(pop, box_box=0)
+        sm.set_state(Q, V, Sx)
+        prm = O.default_params(box_box=0)
+        oq, ov, os_ = Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64)
+        worst = 0.0
+        for chunk in range(4):
+            sm.step(50)
+            gq, _, _, _ = sm.read_state()
+            oq, ov, os_, st, _ = O.run_population(pop, oq, ov, os_, 50, prm=prm, threads=ncores())
+            worst = max(worst, np.abs(gq[:, :3] - oq[:, :3]).max())
+        print(pop.kind, "worst core position error", worst)
+        assert worst <= 1e-4
+
+
+def test_population_mean_fitness_contact_rich():
+    """1024 quadrupeds x 5000 steps: chaos forbids trajectory matching; the
+    population-mean fitness must agree within 2 %."""
+    O = oracle()
+    pop = P.quadrupeds(1024, seed=2).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    sm = _gpu_sim(pop)
+    sm.set_state(Q, V, Sx)
+    sm.step(5000)
+    gf = sm.fitness()
+    _, _, _, gst = sm.read_state()
+    oq, _, _, ost, _ = O.run_population(pop, pop.q0, pop.v0, s0[:, :2 * O.MAXB], 5000, threads=ncores())
+    of = O.fitness(pop.q0, oq)
+    print("mean fitness gpu %.6f oracle %.6f" % (gf.mean(), of.mean()))
+    assert (gst & 5).sum() == 0 and (ost & 5).sum() == 0
+    assert abs(gf.mean() - of.mean()) <= 0.02 * of.mean()
+
+
+def test_status_nonfinite_freezes_only_that_variant():
+    pop = P.quadrupeds(8, seed=2).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    V[3, 7] = np.nan
+    sm = _gpu_sim(pop)
+    sm.set_state(Q, V, Sx)
+    sm.step(20)
+    gq, gv, gs, st = sm.read_state()
+    assert st[3] & S.ST_NONFINITE
+    assert np.array_equal(gq[3], Q[3])
+    others = np.delete(np.arange(8), 3)
+    assert np.all(st[others] & 5 == 0)
+    assert np.all(np.isfinite(gq[others]))
+    assert np.abs(gq[others, :3] - Q[others, :3]).max() > 0  # they moved
+
+
+def test_abi_errors_on_device():
+    sm = S.Sim()
+    with pytest.raises(S.SimError, match="SIM_ESTATE"):
+        sm.step(1)
+    pop = P.quadrupeds(2)
+    bad = pop.subset([0, 1])
+    bad.parent[1, 3] = 5  # parent must precede the child
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        sm.set_population(bad)
+    sm.set_population(pop)
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        sm.read_state(first=1, count=5)
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        sm.step(-1)
+    sm.close()
+
+
+def test_graph_replay_matches_single_launches():
+    """A step count captured as a graph of chunked persistent launches gives
+    the same state as steps issued one by one (bitwise: same kernels)."""
+    pop = P.grammar(64, seed=41).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    a = _gpu_sim(pop, steps_per_launch=7)
+    a.set_state(Q, V, Sx)
+    a.step(40)
+    b = _gpu_sim(pop, steps_per_launch=40)
+    b.set_state(Q, V, Sx)
+    b.step(40)
+    qa, va, _, _ = a.read_state()
+    qb, vb, _, _ = b.read_state()
+    assert np.array_equal(qa, qb) and np.array_equal(va, vb)
+
+
+def test_autotune_keeps_state():
+    pop = P.grammar(200, seed=43).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    a = _gpu_sim(pop)
+    a.set_state(Q, V, Sx)
+    a.autotune(20)
+    q1, v1, _, _ = a.read_state()
+    assert np.array_equal(q1, Q) and np.array_equal(v1, V)
+    a.step(30)
+    b = _gpu_sim(pop, warps_per_block=1)
+    b.set_state(Q, V, Sx)
+    b.step(30)
+    assert np.array_equal(a.read_state()[0], b.read_state()[0])

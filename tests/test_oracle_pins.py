@@ -543,6 +543,29 @@ def test_internal_contact_impulses_conserve_momentum():
     assert seen >= 3
 
 
+def test_zero_jacobian_row_is_frozen():
+    """A planar mechanism (all hinges about x) colliding with itself: the
+    tangent along x has J = 0 (no dof moves the contact point along x), so
+    its impulse stays 0 and the step stays finite."""
+    Rb1 = np.array([[0, -1, 0], [0, 0, 1], [-1, 0, 0]], float)
+    Rb2 = np.array([[0, 1, 0], [-1, 0, 0], [0, 0, 1]], float)
+    m = H.make_model([dict(half=(0.05, 0.05, 0.05), mass=1.0, exclude=0b110),
+                      dict(parent=0, R_fix=Rb1, p_fix=(0, 0, -0.05), com=(0.03, 0, 0), exclude=0b1001),
+                      dict(parent=0, R_fix=Rb2, p_fix=(0, -0.05, 0), com=(0.03, 0, 0), exclude=0b1),
+                      dict(parent=1, R_fix=np.diag([1.0, -1.0, -1.0]), p_fix=(0.06, 0, 0), com=(0.03, 0, 0),
+                           exclude=0b10)])
+    quat = np.array([0.9977, 0.06772, 0.0, 0.0])
+    q = free_q((0.0, 0.0032, 0.16636), quat=quat / np.linalg.norm(quat), hinges=[0.86087, 0.92013, 0.96376])
+    v = np.array([0.0, 0.02, -0.47, 5.0, 0.0, 0.0, 18.7, 13.9, 5.5])
+    c = O.contacts(m, q, O.default_params())
+    assert any(a == 1 and b == 2 for a, b in zip(c["a"], c["b"]))
+    d = O.step_detail(m, q, v, np.zeros(2 * O.MAXB))
+    assert d["status"] == 0 and np.all(np.isfinite(d["v"]))
+    k = [j for j in range(d["nc"]) if c["b"][j] == 2][0]
+    assert c["n"][k][0] == 0.0
+    assert d["lam"][k, 1] == 0.0 and d["lam"][k, 0] > 0.0
+
+
 def test_resting_cube_steady_penetration():
     """Resting flat cube: per-contact impulse m g dt / 4 and steady depth
     d* = kappa A lambda dt / ERP, with A = 1/m + |r x n|^2 / I for a corner."""
