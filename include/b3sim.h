@@ -22,7 +22,8 @@
  *      clipping or an edge-edge point; at most contact_cap contacts (the
  *      deepest, in list order);
  *   7. soft projected Gauss-Seidel over the contact impulses (ERP/CFM soft
- *      constraints, disk friction cone, pgs_iters sweeps, list order);
+ *      constraints, penetration recovery speed capped at max_correct_vel,
+ *      disk friction cone, pgs_iters sweeps, list order);
  *   8. semi-implicit Euler: root position, quaternion exponential map,
  *      hinge angles.
  * Fitness is the core's xy displacement since the start of the run.
@@ -90,6 +91,7 @@ typedef struct {
     int32_t ground;           /* 1: box/plane contacts                       */
     int32_t box_box;          /* 1: box/box contacts inside a robot          */
     int32_t actuate;          /* 1: CPG + PD torques                         */
+    float max_correct_vel;    /* cap of the penetration recovery speed [m/s] */
     int32_t device;           /* CUDA device ordinal                         */
     uint64_t stream;          /* cudaStream_t or 0                           */
     int32_t steps_per_launch; /* persistent chunk; 0: library default        */
@@ -166,6 +168,13 @@ int sim_counters_read(sim_ctx_t* ctx, sim_counters* out);
  * row (-1: ground) in b_out.  *n_out gets the count.  Synchronises. */
 int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* rows,
                        int32_t* b_out, int32_t* n_out);
+
+/* Solver detail of the last step of variant i (caller's order): v_free
+ * (SIM_VW floats, the velocity before contacts) and the contact impulses
+ * (3 floats per contact: normal, tangent 1, tangent 2; room for
+ * 3 * SIM_MAX_CONTACT_CAP floats).  *n_out gets the contact count.
+ * Synchronises. */
+int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out);
 
 /* Human-readable description of the last failure on this context ("" if
  * none).  ctx may be NULL for a failure in sim_create. */

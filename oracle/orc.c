@@ -137,6 +137,7 @@ void orc_default_params(orc_params* p) {
     p->ground = 1;
     p->box_box = 1;
     p->actuate = 1;
+    p->max_correct_vel = 0.1;
 }
 
 static void setup(work* w, const orc_model* m) {
@@ -841,7 +842,14 @@ static int step(work* w, const orc_model* m, const orc_params* prm, double* q, d
             note_margin(w, (a - ORC_AMIN) * 1e4);
             w->A[r] = a > ORC_AMIN ? a : 0.0;
             w->Rs[r] = kappa * a;
-            w->tgt[r] = d == 0 ? erp * w->con.depth[k] / dt : 0.0;
+            if (d == 0) {
+                /* penetration recovery speed, capped (ODE's maximum correcting velocity) */
+                double tn = erp * w->con.depth[k] / dt;
+                note_margin(w, (tn - prm->max_correct_vel) * dt / erp);
+                w->tgt[r] = tn < prm->max_correct_vel ? tn : prm->max_correct_vel;
+            } else {
+                w->tgt[r] = 0.0;
+            }
             FL(w, d == 0 ? 3 : 1);
             w->lam[r] = 0.0;
         }

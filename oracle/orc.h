@@ -68,6 +68,7 @@ typedef struct {
     int32_t ground;             /* box/plane contacts on                    */
     int32_t box_box;            /* box/box contacts on                      */
     int32_t actuate;            /* CPG + PD torques on                      */
+    double max_correct_vel;     /* cap of the penetration recovery speed    */
 } orc_params;
 
 typedef struct {

@@ -200,6 +200,7 @@ int sim_create(const sim_config* cfg, sim_ctx_t** out) {
   }
   if (!(cfg->dt > 0.0) || cfg->pgs_iters < 1 || cfg->contact_cap < 1 || cfg->contact_cap > SIM_MAX_CONTACT_CAP ||
       !(cfg->soft_tau > 0.f) || !(cfg->soft_zeta >= 0.f) || !(cfg->mu >= 0.f) || cfg->steps_per_launch < 0 ||
+      !(cfg->max_correct_vel > 0.f) ||
       !(cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
         cfg->warps_per_block == 4 || cfg->warps_per_block == 8)) {
     g_create_error = "sim_create: configuration out of range";
@@ -248,6 +249,7 @@ int sim_create(const sim_config* cfg, sim_ctx_t** out) {
   P.ground = cfg->ground ? 1 : 0;
   P.box_box = cfg->box_box ? 1 : 0;
   P.actuate = cfg->actuate ? 1 : 0;
+  P.max_correct_vel = cfg->max_correct_vel;
   if (cfg->steps_per_launch > 0) ctx->steps_per_launch = cfg->steps_per_launch;
   if (cfg->warps_per_block > 0) ctx->wpb = cfg->warps_per_block;
   *out = ctx;
@@ -590,6 +592,25 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
     const int b = (ab >> 8) & 0xff;
     b_out[k] = b == 255 ? -1 : b;
   }
+  *n_out = nc;
+  return SIM_OK;
+}
+
+int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_debug_solver: no population");
+  if (i < 0 || i >= ctx->n || !vfree || !lambda || !n_out) return fail(ctx, SIM_EINVAL, "sim_debug_solver: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const int d = ctx->inv[i];
+  int nc = 0;
+  std::vector<float> buf(32 + 4 * b3::kCapMax);
+  CK(cudaMemcpyAsync(&nc, ctx->d_lastnc + d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(buf.data(), ctx->d_scratch + (size_t)d * b3::kScratchFloats + b3::kDbgOffset,
+                     buf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < 32; ++k) vfree[k] = buf[k];
+  for (int k = 0; k < nc; ++k)
+    for (int t = 0; t < 3; ++t) lambda[3 * k + t] = buf[32 + 4 * k + t];
   *n_out = nc;
   return SIM_OK;
 }

@@ -58,10 +58,12 @@ struct StepParams {
   int cap;
   float kp, kd, tau_max, theta_max, armature;
   int ground, box_box, actuate;
+  float max_correct_vel;
 };
 
 // global scratch per variant: candidate rows then Y rows (32 floats each)
-constexpr size_t kScratchFloats = (size_t)kCand * kCandW + (size_t)kYRows * 32;
+constexpr size_t kScratchFloats = (size_t)kCand * kCandW + (size_t)kYRows * 32 + 32 + 4 * kCapMax;
+constexpr size_t kDbgOffset = (size_t)kCand * kCandW + (size_t)kYRows * 32;  // last v_free, then lambda
 
 struct WarpSmem {
   float R[9][32];
@@ -424,6 +426,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   unsigned st = status[var];
   unsigned long long n_contacts = 0, n_narrow = 0, n_broad = 0, n_steps = 0;
   int nc_last = last_nc[var];
+  float vfree_last = 0.f;
 
   float* cand = scratch + (size_t)var * kScratchFloats;
   float* Yg = cand + (size_t)kCand * kCandW;
@@ -489,6 +492,40 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 #pragma unroll
         for (int a = 0; a < 3; ++a)
           r[a] = rp[a] + (Rp[3 * a] * pf[0] + Rp[3 * a + 1] * pf[1] + Rp[3 * a + 2] * pf[2]);
+      }
+    }
+    // FP64 height chain for the ground contacts: the third row of R_b and the
+    // frame-origin height relative to O.  A contact's push-out speed is
+    // ERP * depth / dt with depths of ~0.1 mm, and FP32 kinematics carries
+    // ~5 nm of rounding in heights, which would move a resting robot's
+    // one-step velocity by ~1e-5; heights are therefore evaluated in FP64
+    // (from the FP32 state), everything else stays FP32.
+    double hz0, hz1, hz2, hzb = 0.0;
+    {
+      const double dw = qw, dx = qx, dy = qy, dz = qz;
+      hz0 = 2.0 * (dx * dz - dw * dy);
+      hz1 = 2.0 * (dy * dz + dw * dx);
+      hz2 = 1.0 - 2.0 * (dx * dx + dy * dy);
+      double sd, cd;
+      sincos((double)theta, &sd, &cd);
+      const int k = axis, i = (axis + 1) % 3, j = (axis + 2) % 3;
+      double Ld[9];
+#pragma unroll
+      for (int row = 0; row < 3; ++row) {
+        const double fi = Rf[3 * row + i], fj = Rf[3 * row + j];
+        Ld[3 * row + k] = Rf[3 * row + k];
+        Ld[3 * row + i] = cd * fi + sd * fj;
+        Ld[3 * row + j] = -sd * fi + cd * fj;
+      }
+      for (int lvl = 1; lvl <= maxdepth; ++lvl) {
+        const double p0 = __shfl_sync(kFull, hz0, par0), p1 = __shfl_sync(kFull, hz1, par0);
+        const double p2 = __shfl_sync(kFull, hz2, par0), pb = __shfl_sync(kFull, hzb, par0);
+        if (depth == lvl) {
+          hz0 = p0 * Ld[0] + p1 * Ld[3] + p2 * Ld[6];
+          hz1 = p0 * Ld[1] + p1 * Ld[4] + p2 * Ld[7];
+          hz2 = p0 * Ld[2] + p1 * Ld[5] + p2 * Ld[8];
+          hzb = pb + (p0 * (double)pf[0] + p1 * (double)pf[1] + p2 * (double)pf[2]);
+        }
       }
     }
     float cb[3];
@@ -654,6 +691,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       float acc = upper_solve(sm, y, nv, lane);
       vfree = vd + dt * acc;
       sm.vfree[lane] = lane < nv ? vfree : 0.f;
+      vfree_last = sm.vfree[lane];
     }
 
     // ---------------- 6. contact candidates
@@ -662,14 +700,17 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     if (P.ground) {
       unsigned mask8 = 0;
       float lv[8][3];
+      float zdepth[8];
       if (body) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
 #pragma unroll
           for (int i = 0; i < 3; ++i)
             lv[k][i] = cm[i] + (((k >> i) & 1) ? 1.f : -1.f) * sm.half[i][lane];
-          float z = Oz + (r[2] + (R[6] * lv[k][0] + R[7] * lv[k][1] + R[8] * lv[k][2]));
-          if (z < 0.f) mask8 |= 1u << k;
+          const double z = (double)Oz + (hzb + (hz0 * (double)lv[k][0] + hz1 * (double)lv[k][1] +
+                                                 hz2 * (double)lv[k][2]));
+          if (z < 0.0) mask8 |= 1u << k;
+          zdepth[k] = (float)(-z);
         }
       }
       int cnt = __popc(mask8);
@@ -687,8 +728,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 #pragma unroll
         for (int a = 0; a < 3; ++a)
           pr[a] = r[a] + (R[3 * a] * lv[k][0] + R[3 * a + 1] * lv[k][1] + R[3 * a + 2] * lv[k][2]);
-        float z = Oz + pr[2];
-        if (off < kCand) put_candidate(cand, off, pr, up, -z, lane, 255);
+        if (off < kCand) put_candidate(cand, off, pr, up, zdepth[k], lane, 255);
         ++off;
       }
       ncand = shfi(incl, 31);
@@ -846,7 +886,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         if (dir == 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) yn[i] = y[i];
-          cst[0] = jv - P.erp * depth_k / dt;
+          // penetration recovery speed, capped (ODE's maximum correcting velocity)
+          cst[0] = jv - fminf(P.erp * depth_k / dt, P.max_correct_vel);
           cst[1] = inv;
           cst[2] = Rr;
         } else {
@@ -956,6 +997,14 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     sv[2 * (lane - 1) + 1] = yo;
   }
   if (lane < nv) vv[lane] = vd;
+  // solver detail of the last step (inspection only)
+  float* dbg = scratch + (size_t)var * kScratchFloats + kDbgOffset;
+  dbg[lane] = vfree_last;
+  for (int k = lane; k < nc_last && n_steps > 0; k += 32) {
+    dbg[32 + 4 * k] = sm.lam[k][0];
+    dbg[32 + 4 * k + 1] = sm.lam[k][1];
+    dbg[32 + 4 * k + 2] = sm.lam[k][2];
+  }
 }
 
 }  // namespace b3

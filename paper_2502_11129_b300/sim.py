@@ -25,7 +25,7 @@ STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: 
 
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
            "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
-           "sim_debug_contacts", "sim_last_error"]
+           "sim_debug_contacts", "sim_debug_solver", "sim_last_error"]
 
 
 class SimConfig(C.Structure):
@@ -35,7 +35,7 @@ class SimConfig(C.Structure):
         ("contact_cap", C.c_int32), ("kp", C.c_float), ("kd", C.c_float),
         ("tau_max", C.c_float), ("theta_max", C.c_float), ("armature", C.c_float),
         ("ground", C.c_int32), ("box_box", C.c_int32), ("actuate", C.c_int32),
-        ("device", C.c_int32), ("stream", C.c_uint64), ("steps_per_launch", C.c_int32),
+        ("max_correct_vel", C.c_float), ("device", C.c_int32), ("stream", C.c_uint64), ("steps_per_launch", C.c_int32),
         ("warps_per_block", C.c_int32),
     ]
 
@@ -57,7 +57,7 @@ class Counters(C.Structure):
 
 DEFAULTS = dict(dt=0.002, gravity=(0.0, 0.0, -9.81), pgs_iters=30, soft_tau=0.02, soft_zeta=1.0,
                 mu=1.0, contact_cap=64, kp=2.0, kd=0.05, tau_max=1.0, theta_max=np.pi / 2,
-                armature=1e-4, ground=1, box_box=1, actuate=1, device=0, stream=0,
+                armature=1e-4, ground=1, box_box=1, actuate=1, max_correct_vel=0.1, device=0, stream=0,
                 steps_per_launch=0, warps_per_block=0)
 
 _lib = None
@@ -86,6 +86,7 @@ def lib():
         L.sim_autotune.argtypes = [vp, C.c_int32]
         L.sim_counters_read.argtypes = [vp, P(Counters)]
         L.sim_debug_contacts.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, P(C.c_int32)]
+        L.sim_debug_solver.argtypes = [vp, C.c_int32, vp, vp, P(C.c_int32)]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
@@ -245,3 +246,10 @@ class Sim:
         m = min(n.value, max_contacts)
         return dict(n=n.value, p=rows[:m, 0:3], nrm=rows[:m, 3:6], depth=rows[:m, 6],
                     a=rows[:m, 7].astype(np.int32), b=bb[:m])
+
+    def debug_solver(self, i: int):
+        vfree = np.zeros(SIM_VW, np.float32)
+        lam = np.zeros(3 * SIM_MAX_CONTACT_CAP, np.float32)
+        n = C.c_int32(0)
+        self._check(lib().sim_debug_solver(self.h, i, _ptr(vfree), _ptr(lam), C.byref(n)), "sim_debug_solver")
+        return dict(vfree=vfree, lam=lam[:3 * n.value].reshape(-1, 3), n=n.value)

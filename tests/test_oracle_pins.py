@@ -426,8 +426,14 @@ def _tilted_single_corner(depth=0.001):
 def test_pgs_single_frictionless_contact_closed_form():
     """One contact, mu = 0: Gauss-Seidel converges in one sweep to
     lambda = max(0, (t - J v_free) / (A + R)), and afterwards the soft
-    constraint J v+ - t + R lambda = 0 holds."""
-    m, q, corner = _tilted_single_corner()
+    constraint J v+ - t + R lambda = 0 holds; t = min(ERP depth / dt,
+    max_correct_vel) (below and above the cap)."""
+    _single_contact_case(0.0004, capped=False)
+    _single_contact_case(0.003, capped=True)
+
+
+def _single_contact_case(depth, capped):
+    m, q, corner = _tilted_single_corner(depth)
     v = np.array([0.1, -0.05, -0.5, 0.3, -0.2, 0.1])
     p = O.default_params(mu=0.0)
     d = O.step_detail(m, q, v, np.zeros(2), prm=p)
@@ -455,7 +461,9 @@ def test_pgs_single_frictionless_contact_closed_form():
     kden = p.dt * omg * omg + 2 * p.soft_zeta * omg
     erp = p.dt * omg * omg / kden
     kappa = 1.0 / (p.dt * kden)
-    t = erp * 0.001 / p.dt
+    t = erp * depth / p.dt
+    assert (t > p.max_correct_vel) == capped
+    t = min(t, p.max_correct_vel)
     lam = max(0.0, (t - J @ vfree) / (A + kappa * A))
     assert abs(d["lam"][0, 0] - lam) < 1e-8 * max(lam, 1e-3)
     assert np.allclose(d["lam"][0, 1:], 0.0)
@@ -511,7 +519,7 @@ def test_pgs_single_contact_on_a_hinged_brick():
     kden = p.dt * omg * omg + 2 * p.soft_zeta * omg
     erp = p.dt * omg * omg / kden
     kappa = 1.0 / (p.dt * kden)
-    t = erp * 0.001 / p.dt
+    t = min(erp * 0.001 / p.dt, p.max_correct_vel)
     lam = max(0.0, (t - J @ vfree) / (A + kappa * A))
     assert lam > 0
     assert abs(d["lam"][0, 0] - lam) < 1e-7 * lam
