@@ -147,8 +147,25 @@ __global__ void fitness_kernel(const float* __restrict__ q, const float* __restr
 
 size_t smem_bytes(int wpb) { return (size_t)wpb * sizeof(b3::WarpSmem); }
 
+struct LaunchArgs {
+  const float* mf;
+  const int* mi;
+  const int4* meta;
+  const uint16_t* pairs;
+  float* q;
+  float* v;
+  float* s;
+  unsigned* status;
+  Counters* counters;
+  float* scratch;
+  int* lastnc;
+  int n;
+  StepParams P;
+  cudaStream_t stream;
+};
+
 template <int WPB>
-cudaError_t launch_wpb(sim_ctx* ctx, int nsteps) {
+cudaError_t launch_wpb(const LaunchArgs& a, int nsteps) {
   const size_t sm = smem_bytes(WPB);
   static bool attr_done = false;
   if (!attr_done) {
@@ -156,29 +173,74 @@ cudaError_t launch_wpb(sim_ctx* ctx, int nsteps) {
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  dim3 grid((ctx->n + WPB - 1) / WPB), block(32 * WPB);
-  b3::step_kernel<WPB><<<grid, block, sm, ctx->stream>>>(ctx->d_mf, ctx->d_mi, ctx->d_meta, ctx->d_pairs, ctx->d_q,
-                                                        ctx->d_v, ctx->d_s, ctx->d_status, ctx->d_counters,
-                                                        ctx->d_scratch, ctx->d_lastnc, ctx->n, nsteps, ctx->P);
+  dim3 grid((a.n + WPB - 1) / WPB), block(32 * WPB);
+  b3::step_kernel<WPB><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s, a.status,
+                                                     a.counters, a.scratch, a.lastnc, a.n, nsteps, a.P);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk(sim_ctx* ctx, int nsteps, int wpb) {
+cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb) {
   switch (wpb) {
-    case 1: return launch_wpb<1>(ctx, nsteps);
-    case 2: return launch_wpb<2>(ctx, nsteps);
-    case 4: return launch_wpb<4>(ctx, nsteps);
-    case 8: return launch_wpb<8>(ctx, nsteps);
+    case 1: return launch_wpb<1>(a, nsteps);
+    case 2: return launch_wpb<2>(a, nsteps);
+    case 4: return launch_wpb<4>(a, nsteps);
+    case 8: return launch_wpb<8>(a, nsteps);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, int spl) {
+cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, int spl) {
   for (int done = 0; done < n_steps; done += spl) {
-    cudaError_t e = launch_chunk(ctx, std::min(spl, n_steps - done), wpb);
+    cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+LaunchArgs ctx_args(sim_ctx* ctx) {
+  return LaunchArgs{ctx->d_mf,     ctx->d_mi,       ctx->d_meta,    ctx->d_pairs, ctx->d_q,
+                    ctx->d_v,      ctx->d_s,        ctx->d_status,  ctx->d_counters, ctx->d_scratch,
+                    ctx->d_lastnc, ctx->n,          ctx->P,         ctx->stream};
+}
+
+cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, int spl) {
+  return enqueue_launches(ctx_args(ctx), n_steps, wpb, spl);
+}
+
+bool config_ok(const sim_config* cfg) {
+  return cfg->dt > 0.0 && cfg->pgs_iters >= 1 && cfg->contact_cap >= 1 &&
+         cfg->contact_cap <= SIM_MAX_CONTACT_CAP && cfg->soft_tau > 0.f && cfg->soft_zeta >= 0.f &&
+         cfg->mu >= 0.f && cfg->steps_per_launch >= 0 && cfg->max_correct_vel > 0.f &&
+         (cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
+          cfg->warps_per_block == 4 || cfg->warps_per_block == 8);
+}
+
+// FP32 step constants from a configuration (ERP / CFM of the soft contacts
+// computed in double, then rounded)
+StepParams make_params(const sim_config* cfg) {
+  StepParams P{};
+  const double dt = cfg->dt;
+  const double omg = 2.0 * 3.14159265358979323846 / (double)cfg->soft_tau;
+  const double kden = dt * omg * omg + 2.0 * (double)cfg->soft_zeta * omg;
+  P.dt = (float)dt;
+  P.gx = cfg->gravity[0];
+  P.gy = cfg->gravity[1];
+  P.gz = cfg->gravity[2];
+  P.iters = cfg->pgs_iters;
+  P.mu = cfg->mu;
+  P.erp = (float)(dt * omg * omg / kden);
+  P.kappa = (float)(1.0 / (dt * kden));
+  P.cap = cfg->contact_cap;
+  P.kp = cfg->kp;
+  P.kd = cfg->kd;
+  P.tau_max = cfg->tau_max;
+  P.theta_max = cfg->theta_max;
+  P.armature = cfg->armature;
+  P.ground = cfg->ground ? 1 : 0;
+  P.box_box = cfg->box_box ? 1 : 0;
+  P.actuate = cfg->actuate ? 1 : 0;
+  P.max_correct_vel = cfg->max_correct_vel;
+  return P;
 }
 
 bool finite_all(const float* p, int n) {
@@ -198,11 +260,7 @@ int sim_create(const sim_config* cfg, sim_ctx_t** out) {
     g_create_error = "sim_create: cfg is NULL";
     return SIM_EINVAL;
   }
-  if (!(cfg->dt > 0.0) || cfg->pgs_iters < 1 || cfg->contact_cap < 1 || cfg->contact_cap > SIM_MAX_CONTACT_CAP ||
-      !(cfg->soft_tau > 0.f) || !(cfg->soft_zeta >= 0.f) || !(cfg->mu >= 0.f) || cfg->steps_per_launch < 0 ||
-      !(cfg->max_correct_vel > 0.f) ||
-      !(cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
-        cfg->warps_per_block == 4 || cfg->warps_per_block == 8)) {
+  if (!config_ok(cfg)) {
     g_create_error = "sim_create: configuration out of range";
     return SIM_EINVAL;
   }
@@ -228,28 +286,7 @@ int sim_create(const sim_config* cfg, sim_ctx_t** out) {
     }
     ctx->own_stream = true;
   }
-  StepParams& P = ctx->P;
-  const double dt = cfg->dt;
-  const double omg = 2.0 * 3.14159265358979323846 / (double)cfg->soft_tau;
-  const double kden = dt * omg * omg + 2.0 * (double)cfg->soft_zeta * omg;
-  P.dt = (float)dt;
-  P.gx = cfg->gravity[0];
-  P.gy = cfg->gravity[1];
-  P.gz = cfg->gravity[2];
-  P.iters = cfg->pgs_iters;
-  P.mu = cfg->mu;
-  P.erp = (float)(dt * omg * omg / kden);
-  P.kappa = (float)(1.0 / (dt * kden));
-  P.cap = cfg->contact_cap;
-  P.kp = cfg->kp;
-  P.kd = cfg->kd;
-  P.tau_max = cfg->tau_max;
-  P.theta_max = cfg->theta_max;
-  P.armature = cfg->armature;
-  P.ground = cfg->ground ? 1 : 0;
-  P.box_box = cfg->box_box ? 1 : 0;
-  P.actuate = cfg->actuate ? 1 : 0;
-  P.max_correct_vel = cfg->max_correct_vel;
+  ctx->P = make_params(cfg);
   if (cfg->steps_per_launch > 0) ctx->steps_per_launch = cfg->steps_per_launch;
   if (cfg->warps_per_block > 0) ctx->wpb = cfg->warps_per_block;
   *out = ctx;
