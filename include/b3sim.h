@@ -176,6 +176,66 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
  * Synchronises. */
 int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out);
 
+/* ---- Stepping without any allocation --------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory at the moment they step: code running while a
+ * CUDA graph is being captured (an allocation is not a capturable operation),
+ * hosts whose device memory is owned by another allocator or fixed up front
+ * (game engines, embedded controllers, plugins inside a larger GPU
+ * application), and real-time loops that must not block in the driver.
+ *
+ * sim_step_n_noalloc advances n variants that the CALLER keeps in device
+ * memory it already owns, using the same step kernel as sim_step_n.  It calls
+ * no cudaMalloc, cudaFree or allocating library routine.  Its per-variant
+ * scratch (contact candidates and contact Jacobian rows, about 34 KB per
+ * variant) is a fixed array inside this library: SIM_NOALLOC_MAX_VARIANTS
+ * variants, about 2.2 MB, held by every device that loads the library until
+ * the process exits.  Larger n is rejected with SIM_EINVAL.
+ *   - cfg->device is made current; cfg->stream (0: the legacy default
+ *     stream) receives the work, asynchronously.
+ *   - The first call on a device looks up the scratch's device address; make
+ *     that first call before any stream capture on that device.
+ *   - All calls share the one scratch array, which keeps the last call's
+ *     contents; calls whose work overlaps on the GPU (other streams, other
+ *     host threads) race on it and must be serialised by the caller.
+ *   - Variants are stepped in the order given (no size sorting).
+ * Device layout expected in *pop (all device pointers, caller-owned):
+ *   model_f  n x SIM_MODEL_NF x 32 floats, [variant][field][body slot]:
+ *            joint frame R (9, row-major), joint frame p (3), half size (3),
+ *            box centre (3), mass, principal inertia about the box centre
+ *            (3: m(hy^2+hz^2)/3, m(hx^2+hz^2)/3, m(hx^2+hy^2)/3), CPG weight,
+ *            CPG coupling, bounding radius |half size|; slots >= n_bodies
+ *            hold R = identity and zeros.
+ *   model_i  n x SIM_MODEL_NI x 32 int32: parent (-1 for body 0 and unused
+ *            slots), hinge axis, path mask (bit j for every body on the path
+ *            from body 0 to this body, both ends included), child mask, depth
+ *            (body 0: 0).
+ *   meta     n x 4 int32: n_bodies, maximum depth, pair count, offset of the
+ *            variant's pairs in `pairs`.
+ *   pairs    uint16 (a << 8) | b for every body pair a < b that may collide
+ *            (b's parent is not a, and neither excludes the other).
+ *   q, v, cpg, status  state rows with strides 32, 32, 64 floats and one
+ *            uint32 status word per variant (as in sim_read_state).
+ * Returns SIM_OK, SIM_EINVAL (bad argument; sim_last_error(NULL) says which)
+ * or SIM_ECUDA. */
+#define SIM_NOALLOC_MAX_VARIANTS 64
+#define SIM_MODEL_NF 25
+#define SIM_MODEL_NI 5
+
+typedef struct {
+    int32_t n;                /* variants, 1..SIM_NOALLOC_MAX_VARIANTS        */
+    const float* model_f;
+    const int32_t* model_i;
+    const int32_t* meta;
+    const uint16_t* pairs;
+    float* q;
+    float* v;
+    float* cpg;
+    uint32_t* status;
+} sim_device_population;
+
+int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, int32_t n_steps);
+
 /* Human-readable description of the last failure on this context ("" if
  * none).  ctx may be NULL for a failure in sim_create. */
 const char* sim_last_error(const sim_ctx_t* ctx);

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -249,9 +250,105 @@ bool finite_all(const float* p, int n) {
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free stepping.  The step kernel needs per-variant global scratch
+// (contact candidates, contact Jacobian rows); here it lives in file-scope
+// device arrays sized for SIM_NOALLOC_MAX_VARIANTS variants, which every
+// device that loads this library keeps until the process exits.  In host code
+// these names are host-side stand-ins, not device addresses, so the device
+// addresses are looked up once per device and passed to the kernel.
+static __device__ __align__(256) float g_noalloc_scratch[SIM_NOALLOC_MAX_VARIANTS * b3::kScratchFloats];
+static __device__ __align__(256) Counters g_noalloc_counters[SIM_NOALLOC_MAX_VARIANTS];
+static __device__ __align__(256) int g_noalloc_lastnc[SIM_NOALLOC_MAX_VARIANTS];
+
+constexpr int kMaxDevices = 64;
+struct NoallocAddrs {
+  bool ready = false;
+  float* scratch = nullptr;
+  Counters* counters = nullptr;
+  int* lastnc = nullptr;
+};
+NoallocAddrs g_noalloc[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// once per device, with that device current
+cudaError_t noalloc_setup(int dev, NoallocAddrs* out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoallocAddrs& a = g_noalloc[dev];
+  if (!a.ready) {
+    cudaError_t e = cudaGetSymbolAddress((void**)&a.scratch, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress((void**)&a.counters, g_noalloc_counters);
+    if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress((void**)&a.lastnc, g_noalloc_lastnc);
+    if (e != cudaSuccess) return e;
+    a.ready = true;
+  }
+  *out = a;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
+
+int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, int32_t n_steps) {
+  if (!cfg || !pop) {
+    g_create_error = "sim_step_n_noalloc: cfg or pop is NULL";
+    return SIM_EINVAL;
+  }
+  if (!config_ok(cfg)) {
+    g_create_error = "sim_step_n_noalloc: configuration out of range";
+    return SIM_EINVAL;
+  }
+  if (pop->n < 1 || pop->n > SIM_NOALLOC_MAX_VARIANTS) {
+    g_create_error = "sim_step_n_noalloc: n must be 1..SIM_NOALLOC_MAX_VARIANTS (64): the static scratch holds 64 variants";
+    return SIM_EINVAL;
+  }
+  if (n_steps < 0) {
+    g_create_error = "sim_step_n_noalloc: n_steps < 0";
+    return SIM_EINVAL;
+  }
+  if (!pop->model_f || !pop->model_i || !pop->meta || !pop->pairs || !pop->q || !pop->v || !pop->cpg ||
+      !pop->status) {
+    g_create_error = "sim_step_n_noalloc: a device pointer is NULL";
+    return SIM_EINVAL;
+  }
+  if (cfg->device < 0 || cfg->device >= kMaxDevices) {
+    g_create_error = "sim_step_n_noalloc: device ordinal out of range";
+    return SIM_EINVAL;
+  }
+  if (n_steps == 0) return SIM_OK;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  NoallocAddrs a;
+  if (e == cudaSuccess) e = noalloc_setup(cfg->device, &a);
+  if (e != cudaSuccess) {
+    g_create_error_buf = std::string("sim_step_n_noalloc: ") + cudaGetErrorString(e);
+    g_create_error = g_create_error_buf.c_str();
+    return SIM_ECUDA;
+  }
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+  const size_t n = (size_t)pop->n;
+  // counters and the last-step contact counts start at zero on every call;
+  // the rest of the scratch is written before it is read within each step
+  e = cudaMemsetAsync(a.counters, 0, n * sizeof(Counters), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.lastnc, 0, n * sizeof(int), stream);
+  if (e == cudaSuccess) {
+    LaunchArgs args{pop->model_f, pop->model_i, reinterpret_cast<const int4*>(pop->meta), pop->pairs,
+                    pop->q,       pop->v,       pop->cpg, pop->status, a.counters, a.scratch, a.lastnc,
+                    pop->n,       make_params(cfg), stream};
+    const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
+    const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : 500;
+    e = enqueue_launches(args, n_steps, wpb, spl);
+  }
+  if (e != cudaSuccess) {
+    g_create_error_buf = std::string("sim_step_n_noalloc: ") + cudaGetErrorString(e);
+    g_create_error = g_create_error_buf.c_str();
+    return SIM_ECUDA;
+  }
+  return SIM_OK;
+}
+
 
 int sim_create(const sim_config* cfg, sim_ctx_t** out) {
   if (!out) return SIM_EINVAL;

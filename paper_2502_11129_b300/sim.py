@@ -25,7 +25,7 @@ STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: 
 
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
            "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
-           "sim_debug_contacts", "sim_debug_solver", "sim_last_error"]
+           "sim_debug_contacts", "sim_debug_solver", "sim_step_n_noalloc", "sim_last_error"]
 
 
 class SimConfig(C.Structure):
@@ -48,6 +48,13 @@ class VariantDesc(C.Structure):
         ("mass", C.POINTER(C.c_float)), ("cpg_w_internal", C.POINTER(C.c_float)),
         ("cpg_w_couple", C.POINTER(C.c_float)),
     ]
+
+
+class DevicePopulation(C.Structure):
+    """Caller-owned device buffers for sim_step_n_noalloc (see b3sim.h)."""
+    _fields_ = [("n", C.c_int32), ("model_f", C.c_void_p), ("model_i", C.c_void_p),
+                ("meta", C.c_void_p), ("pairs", C.c_void_p), ("q", C.c_void_p), ("v", C.c_void_p),
+                ("cpg", C.c_void_p), ("status", C.c_void_p)]
 
 
 class Counters(C.Structure):
@@ -87,6 +94,7 @@ def lib():
         L.sim_counters_read.argtypes = [vp, P(Counters)]
         L.sim_debug_contacts.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, P(C.c_int32)]
         L.sim_debug_solver.argtypes = [vp, C.c_int32, vp, vp, P(C.c_int32)]
+        L.sim_step_n_noalloc.argtypes = [P(SimConfig), P(DevicePopulation), C.c_int32]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
