@@ -120,6 +120,8 @@ typedef struct {
     double narrow_pairs;      /* box/box pairs through the narrow phase      */
     double broad_pairs;       /* box/box pairs through the broad phase       */
     double variant_steps;     /* variants x steps advanced                   */
+    double sm_cycles;         /* sum over variants of SM clock cycles spent
+                                 in the step loop (per-warp clock64)         */
 } sim_counters;
 
 /* Create a context on cfg->device.  Copies cfg.  *out is NULL on failure. */
@@ -173,8 +175,13 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
  * (SIM_VW floats, the velocity before contacts) and the contact impulses
  * (3 floats per contact: normal, tangent 1, tangent 2; room for
  * 3 * SIM_MAX_CONTACT_CAP floats).  *n_out gets the contact count.
- * Synchronises. */
-int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out);
+ * cycles_per_step (may be NULL, else 11 floats) gets the SM clock cycles per
+ * step that the variant's warp spent in its last launch: [0] the whole step,
+ * [1..10] its phases (CPG + FK, inertias + RNEA + CRBA, Cholesky + v_free,
+ * ground contacts, box/box contacts, contact cap, contact rows, Gauss-Seidel,
+ * integration, unused).  Synchronises. */
+int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out,
+                     float* cycles_per_step);
 
 /* ---- Stepping without any allocation --------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
@@ -187,9 +194,9 @@ int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int
  * sim_step_n_noalloc advances n variants that the CALLER keeps in device
  * memory it already owns, using the same step kernel as sim_step_n.  It calls
  * no cudaMalloc, cudaFree or allocating library routine.  Its per-variant
- * scratch (contact candidates and contact Jacobian rows, about 34 KB per
- * variant) is a fixed array inside this library: SIM_NOALLOC_MAX_VARIANTS
- * variants, about 2.2 MB, held by every device that loads the library until
+ * scratch (contact candidates, narrow-phase staging rows, contact
+ * Jacobian rows and Gauss-Seidel constants, about 45 KB per variant) is a fixed array inside this library: SIM_NOALLOC_MAX_VARIANTS
+ * variants, about 2.9 MB, held by every device that loads the library until
  * the process exits.  Larger n is rejected with SIM_EINVAL.
  *   - cfg->device is made current; cfg->stream (0: the legacy default
  *     stream) receives the work, asynchronously.

@@ -694,6 +694,7 @@ int sim_counters_read(sim_ctx_t* ctx, sim_counters* out) {
     r.narrow_pairs += (double)c.narrow;
     r.broad_pairs += (double)c.broad;
     r.variant_steps += (double)c.steps;
+    r.sm_cycles += (double)c.cycles;
   }
   *out = r;
   return SIM_OK;
@@ -730,19 +731,25 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
   return SIM_OK;
 }
 
-int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out) {
+int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out,
+                     float* cycles_per_step) {
   if (!ctx) return SIM_EINVAL;
   if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_debug_solver: no population");
   if (i < 0 || i >= ctx->n || !vfree || !lambda || !n_out) return fail(ctx, SIM_EINVAL, "sim_debug_solver: bad arguments");
   CK(cudaSetDevice(ctx->cfg.device));
   const int d = ctx->inv[i];
   int nc = 0;
-  std::vector<float> buf(32 + 4 * b3::kCapMax);
+  std::vector<float> buf(32 + 4 * b3::kCapMax + 16);
   CK(cudaMemcpyAsync(&nc, ctx->d_lastnc + d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(buf.data(), ctx->d_scratch + (size_t)d * b3::kScratchFloats + b3::kDbgOffset,
                      buf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  for (int k = 0; k < 32; ++k) vfree[k] = buf[k];
+  for (int k = 0; k < 31; ++k) vfree[k] = buf[k];
+  vfree[31] = 0.f;
+  if (cycles_per_step) {
+    cycles_per_step[0] = buf[31];
+    for (int k = 0; k < b3::kPhases; ++k) cycles_per_step[1 + k] = buf[32 + 4 * b3::kCapMax + k];
+  }
   for (int k = 0; k < nc; ++k)
     for (int t = 0; t < 3; ++t) lambda[3 * k + t] = buf[32 + 4 * k + t];
   *n_out = nc;

@@ -12,7 +12,7 @@
 //   * lane = row     for the Cholesky trailing update;
 //   * lane = dof     for the triangular solves and the Gauss-Seidel sweeps;
 //   * lane = contact for building contact Jacobian rows;
-//   * lane = axis    for the 15 separating-axis tests of a box/box pair.
+//   * lane = pair    for the box/box broad and narrow phases.
 //
 // Gauss-Seidel runs in the Cholesky-transformed velocity u = L^T (v - v_free):
 // with Y_r = L^-1 J_r^T, the row residual J_r v = J_r v_free + Y_r . u and the
@@ -27,7 +27,7 @@ namespace b3 {
 
 constexpr int kMaxB = 26;       // bodies per robot
 constexpr int kMaxV = 31;       // dofs per robot
-constexpr int kLs = 33;         // row stride of M / L in shared memory
+constexpr int kTri = 32 * 33 / 2;  // packed lower triangle of M / L (row i at i(i+1)/2)
 constexpr int kCapMax = 64;     // contacts kept per step
 constexpr int kCand = 256;      // contact candidates per step
 constexpr int kCandW = 8;       // floats per candidate row
@@ -61,26 +61,30 @@ struct StepParams {
   float max_correct_vel;
 };
 
-// global scratch per variant: candidate rows then Y rows (32 floats each)
-constexpr size_t kScratchFloats = (size_t)kCand * kCandW + (size_t)kYRows * 32 + 32 + 4 * kCapMax;
-constexpr size_t kDbgOffset = (size_t)kCand * kCandW + (size_t)kYRows * 32;  // last v_free, then lambda
+// global scratch per variant: candidate rows, the narrow phase's per-lane
+// staging rows, Y rows (32 floats each), the
+// Gauss-Seidel constants of each contact (12 floats), then the last step's
+// v_free and impulses (inspection only)
+constexpr size_t kStageOffset = (size_t)kCand * kCandW;            // 32 lanes x 8 points x 8 floats
+constexpr size_t kYOffset = kStageOffset + (size_t)32 * 8 * kCandW;
+constexpr size_t kCstOffset = kYOffset + (size_t)kYRows * 32;
+constexpr size_t kDbgOffset = kCstOffset + (size_t)kCapMax * 12;
+constexpr int kPhases = 10;  // per-phase cycle counters (inspection only)
+constexpr size_t kScratchFloats = kDbgOffset + 32 + 4 * kCapMax + 16;
+
+__device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
 
 struct WarpSmem {
-  float R[9][32];
-  float r[3][32];
-  float c[3][32];
-  float half[3][32];
-  float rad[32];
+  float R[9][32];          // body rotations (lane = body)
+  float r[3][32];          // body frame origins relative to the core origin
+  float c[3][32];          // box centres relative to the core origin
   float S[6][32];          // dof-indexed motion subspace columns
   float acc[16][32];       // per-body f (6) + composite inertia (10)
-  float M[32 * kLs];       // mass matrix, then its Cholesky factor (lower)
+  float M[kTri];           // mass matrix, then its Cholesky factor (packed lower)
   float invd[32];
   float vfree[32];
   int parent[32];
   unsigned path[32];
-  float poly[2][8][3];     // clipping buffers (lane 0)
-  float cst[kCapMax][12];  // per-contact Gauss-Seidel constants
-  float lam[kCapMax][4];
   unsigned keep[kCand / 32];
 };
 
@@ -91,6 +95,25 @@ __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
+}
+
+// Sums of three per-lane values over the warp, delivered to every lane.
+// Pairs of values travel together in the first two butterfly levels, so
+// three sums cost 9 shuffles instead of 15.
+__device__ __forceinline__ void warp_sum3(float& a, float& b, float& c, int lane) {
+  const bool h16 = (lane & 16) != 0;
+  const float r0 = __shfl_xor_sync(kFull, h16 ? a : c, 16);
+  const float r1 = __shfl_xor_sync(kFull, h16 ? b : 0.f, 16);
+  const float x0 = (h16 ? c : a) + r0;  // lanes < 16: a, lanes >= 16: c
+  const float x1 = (h16 ? 0.f : b) + r1;  // lanes < 16: b, lanes >= 16: 0
+  const bool h8 = (lane & 8) != 0;
+  float y = (h8 ? x1 : x0) + __shfl_xor_sync(kFull, h8 ? x0 : x1, 8);
+  y += __shfl_xor_sync(kFull, y, 4);
+  y += __shfl_xor_sync(kFull, y, 2);
+  y += __shfl_xor_sync(kFull, y, 1);
+  a = __shfl_sync(kFull, y, 0);
+  b = __shfl_sync(kFull, y, 8);
+  c = __shfl_sync(kFull, y, 16);
 }
 
 __device__ __forceinline__ float dot3(const float* a, const float* b) {
@@ -148,7 +171,7 @@ __device__ __forceinline__ float lower_solve(const WarpSmem& sm, float b, int nv
   for (int i = 0; i < nv; ++i) {
     float yi = shf(acc, i) * sm.invd[i];
     if (lane == i) y = yi;
-    if (lane > i && lane < nv) acc -= sm.M[lane * kLs + i] * yi;
+    if (lane > i && lane < nv) acc -= sm.M[tri(lane) + i] * yi;
   }
   return y;
 }
@@ -159,7 +182,7 @@ __device__ __forceinline__ float upper_solve(const WarpSmem& sm, float y, int nv
   for (int i = nv - 1; i >= 0; --i) {
     float xi = shf(acc, i) * sm.invd[i];
     if (lane == i) x = xi;
-    if (lane < i) acc -= sm.M[i * kLs + lane] * xi;
+    if (lane < i) acc -= sm.M[tri(i) + lane] * xi;
   }
   return x;
 }
@@ -177,183 +200,171 @@ __device__ __forceinline__ void put_candidate(float* cand, int n, const float* p
   row[7] = __int_as_float((a & 0xff) | ((b & 0xff) << 8));
 }
 
-// Box/box narrow phase of bodies a < b: separating-axis test over 15 axes
-// (lane = axis), then face clipping or the edge-edge point on lane 0.
-// Appends to the candidate list; returns the new count (warp-uniform).
-__device__ int box_box_pair(WarpSmem& sm, float* cand, int n, int a, int b, int lane, unsigned& st) {
+// Box/box narrow phase of one body pair a < b on one lane: separating-axis
+// test over 15 axes (faces of a, faces of b, edge crosses), then face
+// clipping or the edge-edge point.  Up to 8 contact rows go to `out`
+// (8 floats each, candidate layout); returns their count.  Axis choice:
+// minimum overlap, ties to the lowest index, a face unless the best edge
+// overlap is below 0.95 x the best face overlap.  Normals point from b to a.
+__device__ __noinline__ int box_box_lane(const WarpSmem& sm, const float* __restrict__ F, int a, int b, float* out) {
   float Ax[3][3], Bx[3][3], hA[3], hB[3], D[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     axis_of(sm, a, k, Ax[k]);
     axis_of(sm, b, k, Bx[k]);
-    hA[k] = sm.half[k][a];
-    hB[k] = sm.half[k][b];
+    hA[k] = __ldg(F + (F_HALF + k) * 32 + a);
+    hB[k] = __ldg(F + (F_HALF + k) * 32 + b);
     D[k] = sm.c[k][b] - sm.c[k][a];
   }
-  float L[3] = {0.f, 0.f, 0.f};
-  bool valid = lane < 15;
-  if (lane < 3) {
-    L[0] = Ax[lane][0]; L[1] = Ax[lane][1]; L[2] = Ax[lane][2];
-  } else if (lane < 6) {
-    L[0] = Bx[lane - 3][0]; L[1] = Bx[lane - 3][1]; L[2] = Bx[lane - 3][2];
-  } else if (lane < 15) {
-    int i = (lane - 6) / 3, j = (lane - 6) % 3;
-    cross3(Ax[i], Bx[j], L);
-    float nl = sqrtf(dot3(L, L));
-    if (nl < 1e-6f) valid = false;
-    else { L[0] /= nl; L[1] /= nl; L[2] /= nl; }
+  float fbest = 0.f, ebest = 0.f, min_ov = 0.f;
+  int fi = -1, ei = -1;
+  float Le[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int e = 0; e < 15; ++e) {
+    float L[3];
+    bool valid = true;
+    if (e < 3) {
+      L[0] = Ax[e][0]; L[1] = Ax[e][1]; L[2] = Ax[e][2];
+    } else if (e < 6) {
+      L[0] = Bx[e - 3][0]; L[1] = Bx[e - 3][1]; L[2] = Bx[e - 3][2];
+    } else {
+      cross3(Ax[(e - 6) / 3], Bx[(e - 6) % 3], L);
+      const float nl = sqrtf(dot3(L, L));
+      if (nl < 1e-6f) valid = false;
+      else { L[0] /= nl; L[1] /= nl; L[2] /= nl; }
+    }
+    if (valid) {
+      float rA = 0.f, rB = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        rA += hA[k] * fabsf(dot3(Ax[k], L));
+        rB += hB[k] * fabsf(dot3(Bx[k], L));
+      }
+      const float ov = rA + rB - fabsf(dot3(D, L));
+      if (e == 0 || ov < min_ov) min_ov = ov;
+      if (e < 6) {
+        if (fi < 0 || ov < fbest) { fbest = ov; fi = e; }
+      } else if (ei < 0 || ov < ebest) {
+        ebest = ov; ei = e;
+        Le[0] = L[0]; Le[1] = L[1]; Le[2] = L[2];
+      }
+    }
   }
-  float ov = __int_as_float(0x7f800000);  // +inf
-  if (valid) {
-    float rA = 0.f, rB = 0.f;
+  if (!(min_ov > 0.f)) return 0;
+  const bool use_edge = ei >= 0 && ebest < 0.95f * fbest;
+  const int ab = (a & 0xff) | ((b & 0xff) << 8);
+  if (!use_edge) {
+    const bool refA = fi < 3;
+    const int ri = refA ? fi : fi - 3;
+    float Rx[3][3], Ix[3][3], hR[3], hI[3], cR[3], cI[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      rA += hA[k] * fabsf(dot3(Ax[k], L));
-      rB += hB[k] * fabsf(dot3(Bx[k], L));
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        Rx[k][t] = refA ? Ax[k][t] : Bx[k][t];
+        Ix[k][t] = refA ? Bx[k][t] : Ax[k][t];
+      }
+      hR[k] = refA ? hA[k] : hB[k];
+      hI[k] = refA ? hB[k] : hA[k];
+      cR[k] = refA ? sm.c[k][a] : sm.c[k][b];
+      cI[k] = refA ? sm.c[k][b] : sm.c[k][a];
     }
-    ov = rA + rB - fabsf(dot3(D, L));
-  }
-  float mn = ov;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(kFull, mn, o));
-  if (!(mn > 0.f)) return n;
-  // best face (lanes 0..5) and best edge (lanes 6..14), ties to the lowest index
-  float fv = lane < 6 ? ov : __int_as_float(0x7f800000);
-  int fi = lane;
-  float ev = (lane >= 6 && lane < 15 && valid) ? ov : __int_as_float(0x7f800000);
-  int ei = lane;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    float fv2 = __shfl_xor_sync(kFull, fv, o);
-    int fi2 = __shfl_xor_sync(kFull, fi, o);
-    if (fv2 < fv || (fv2 == fv && fi2 < fi)) { fv = fv2; fi = fi2; }
-    float ev2 = __shfl_xor_sync(kFull, ev, o);
-    int ei2 = __shfl_xor_sync(kFull, ei, o);
-    if (ev2 < ev || (ev2 == ev && ei2 < ei)) { ev = ev2; ei = ei2; }
-  }
-  const bool has_edge = ev < __int_as_float(0x7f800000);
-  const bool use_edge = has_edge && ev < 0.95f * fv;
-  float Le[3];
-  {
-    int src = use_edge ? ei : 0;
-    Le[0] = shf(L[0], src); Le[1] = shf(L[1], src); Le[2] = shf(L[2], src);
-  }
-  int added = 0;
-  if (lane == 0) {
-    if (!use_edge) {
-      const bool refA = fi < 3;
-      const int ri = refA ? fi : fi - 3;
-      float Rx[3][3], Ix[3][3], hR[3], hI[3], cR[3], cI[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          Rx[k][t] = refA ? Ax[k][t] : Bx[k][t];
-          Ix[k][t] = refA ? Bx[k][t] : Ax[k][t];
-        }
-        hR[k] = refA ? hA[k] : hB[k];
-        hI[k] = refA ? hB[k] : hA[k];
-        cR[k] = refA ? sm.c[k][a] : sm.c[k][b];
-        cI[k] = refA ? sm.c[k][b] : sm.c[k][a];
-      }
-      float toI[3] = {cI[0] - cR[0], cI[1] - cR[1], cI[2] - cR[2]};
-      float rax[3] = {Rx[ri][0], Rx[ri][1], Rx[ri][2]};
-      float sg = dot3(toI, rax) >= 0.f ? 1.f : -1.f;
-      float nref[3] = {sg * rax[0], sg * rax[1], sg * rax[2]};
-      float dd[3];
-      for (int k = 0; k < 3; ++k) dd[k] = dot3(Ix[k], nref);
-      int ki = 0;
-      for (int k = 1; k < 3; ++k) if (fabsf(dd[k]) > fabsf(dd[ki])) ki = k;
-      float si = dd[ki] > 0.f ? -1.f : 1.f;
-      int k1 = (ki + 1) % 3, k2 = (ki + 2) % 3;
-      if (k1 > k2) { int t = k1; k1 = k2; k2 = t; }
-      float fc[3];
-      for (int k = 0; k < 3; ++k) fc[k] = cI[k] + si * hI[ki] * Ix[ki][k];
-      const float s1[4] = {1.f, -1.f, -1.f, 1.f}, s2[4] = {1.f, 1.f, -1.f, -1.f};
-      int np = 4, cur = 0;
-      for (int v = 0; v < 4; ++v)
-        for (int k = 0; k < 3; ++k)
-          sm.poly[0][v][k] = fc[k] + s1[v] * hI[k1] * Ix[k1][k] + s2[v] * hI[k2] * Ix[k2][k];
-      int u1 = (ri + 1) % 3, u2 = (ri + 2) % 3;
-      if (u1 > u2) { int t = u1; u1 = u2; u2 = t; }
-      for (int pl = 0; pl < 4 && np > 0; ++pl) {
-        const int ax = pl < 2 ? u1 : u2;
-        const float ps = (pl & 1) ? -1.f : 1.f;
-        float u[3] = {Rx[ax][0], Rx[ax][1], Rx[ax][2]};
-        const float e = hR[ax];
-        float dist[8];
-        for (int v = 0; v < np; ++v) {
-          float rel[3] = {sm.poly[cur][v][0] - cR[0], sm.poly[cur][v][1] - cR[1], sm.poly[cur][v][2] - cR[2]};
-          dist[v] = ps * dot3(rel, u) - e;
-        }
-        int no = 0;
-        for (int v = 0; v < np; ++v) {
-          int nx = (v + 1) % np;
-          bool in_v = dist[v] <= 0.f, in_n = dist[nx] <= 0.f;
-          // at most 8 vertices: a convex quad gains at most one per plane;
-          // spurious crossings from rounding past 8 are dropped
-          if (in_v && no < 8) {
-            for (int k = 0; k < 3; ++k) sm.poly[cur ^ 1][no][k] = sm.poly[cur][v][k];
-            ++no;
-          }
-          if (in_v != in_n && no < 8) {
-            float t = dist[v] / (dist[v] - dist[nx]);
-            for (int k = 0; k < 3; ++k)
-              sm.poly[cur ^ 1][no][k] = sm.poly[cur][v][k] + t * (sm.poly[cur][nx][k] - sm.poly[cur][v][k]);
-            ++no;
-          }
-        }
-        np = no;
-        cur ^= 1;
-      }
-      float nrm[3];
-      for (int k = 0; k < 3; ++k) nrm[k] = refA ? -nref[k] : nref[k];
+    const float toI[3] = {cI[0] - cR[0], cI[1] - cR[1], cI[2] - cR[2]};
+    const float rax[3] = {Rx[ri][0], Rx[ri][1], Rx[ri][2]};
+    const float sg = dot3(toI, rax) >= 0.f ? 1.f : -1.f;
+    const float nref[3] = {sg * rax[0], sg * rax[1], sg * rax[2]};
+    float dd[3];
+    for (int k = 0; k < 3; ++k) dd[k] = dot3(Ix[k], nref);
+    int ki = 0;
+    for (int k = 1; k < 3; ++k) if (fabsf(dd[k]) > fabsf(dd[ki])) ki = k;
+    const float si = dd[ki] > 0.f ? -1.f : 1.f;
+    int k1 = (ki + 1) % 3, k2 = (ki + 2) % 3;
+    if (k1 > k2) { const int t = k1; k1 = k2; k2 = t; }
+    float fc[3];
+    for (int k = 0; k < 3; ++k) fc[k] = cI[k] + si * hI[ki] * Ix[ki][k];
+    const float s1[4] = {1.f, -1.f, -1.f, 1.f}, s2[4] = {1.f, 1.f, -1.f, -1.f};
+    float poly[2][8][3];
+    int np = 4, cur = 0;
+    for (int v = 0; v < 4; ++v)
+      for (int k = 0; k < 3; ++k)
+        poly[0][v][k] = fc[k] + s1[v] * hI[k1] * Ix[k1][k] + s2[v] * hI[k2] * Ix[k2][k];
+    int u1 = (ri + 1) % 3, u2 = (ri + 2) % 3;
+    if (u1 > u2) { const int t = u1; u1 = u2; u2 = t; }
+    for (int pl = 0; pl < 4 && np > 0; ++pl) {
+      const int ax = pl < 2 ? u1 : u2;
+      const float ps = (pl & 1) ? -1.f : 1.f;
+      const float u[3] = {Rx[ax][0], Rx[ax][1], Rx[ax][2]};
+      const float eh = hR[ax];
+      float dist[8];
       for (int v = 0; v < np; ++v) {
-        float pt[3] = {sm.poly[cur][v][0], sm.poly[cur][v][1], sm.poly[cur][v][2]};
-        float rel[3] = {pt[0] - cR[0], pt[1] - cR[1], pt[2] - cR[2]};
-        float depth = hR[ri] - dot3(rel, nref);
-        if (depth > 0.f) {
-          if (n + added < kCand) put_candidate(cand, n + added, pt, nrm, depth, a, b);
-          else st |= 8u;
-          ++added;
+        const float rel[3] = {poly[cur][v][0] - cR[0], poly[cur][v][1] - cR[1], poly[cur][v][2] - cR[2]};
+        dist[v] = ps * dot3(rel, u) - eh;
+      }
+      int no = 0;
+      for (int v = 0; v < np; ++v) {
+        const int nx = (v + 1) % np;
+        const bool in_v = dist[v] <= 0.f, in_n = dist[nx] <= 0.f;
+        // at most 8 vertices: a convex quad gains at most one per plane;
+        // spurious crossings from rounding past 8 are dropped
+        if (in_v && no < 8) {
+          for (int k = 0; k < 3; ++k) poly[cur ^ 1][no][k] = poly[cur][v][k];
+          ++no;
+        }
+        if (in_v != in_n && no < 8) {
+          const float t = dist[v] / (dist[v] - dist[nx]);
+          for (int k = 0; k < 3; ++k) poly[cur ^ 1][no][k] = poly[cur][v][k] + t * (poly[cur][nx][k] - poly[cur][v][k]);
+          ++no;
         }
       }
-    } else {
-      const int i = (ei - 6) / 3, j = (ei - 6) % 3;
-      float Lv[3] = {Le[0], Le[1], Le[2]};
-      if (dot3(D, Lv) < 0.f) { Lv[0] = -Lv[0]; Lv[1] = -Lv[1]; Lv[2] = -Lv[2]; }
-      float PA[3], PB[3];
-      for (int k = 0; k < 3; ++k) { PA[k] = sm.c[k][a]; PB[k] = sm.c[k][b]; }
-      for (int k = 0; k < 3; ++k) {
-        if (k != i) {
-          float s = dot3(Ax[k], Lv) >= 0.f ? hA[k] : -hA[k];
-          for (int t = 0; t < 3; ++t) PA[t] += s * Ax[k][t];
-        }
-        if (k != j) {
-          float s = dot3(Bx[k], Lv) >= 0.f ? hB[k] : -hB[k];
-          for (int t = 0; t < 3; ++t) PB[t] -= s * Bx[k][t];
-        }
+      np = no;
+      cur ^= 1;
+    }
+    int n = 0;
+    for (int v = 0; v < np; ++v) {
+      const float rel[3] = {poly[cur][v][0] - cR[0], poly[cur][v][1] - cR[1], poly[cur][v][2] - cR[2]};
+      const float depth = hR[ri] - dot3(rel, nref);
+      if (depth > 0.f) {
+        float* row = out + (size_t)n * kCandW;
+        row[0] = poly[cur][v][0]; row[1] = poly[cur][v][1]; row[2] = poly[cur][v][2];
+        row[3] = refA ? -nref[0] : nref[0];
+        row[4] = refA ? -nref[1] : nref[1];
+        row[5] = refA ? -nref[2] : nref[2];
+        row[6] = depth;
+        row[7] = __int_as_float(ab);
+        ++n;
       }
-      float wv[3] = {PA[0] - PB[0], PA[1] - PB[1], PA[2] - PB[2]};
-      float bb = dot3(Ax[i], Bx[j]);
-      float dd = dot3(Ax[i], wv);
-      float ee = dot3(Bx[j], wv);
-      float den = 1.f - bb * bb;
-      float s = (bb * ee - dd) / den;
-      float t = (ee - bb * dd) / den;
-      s = fminf(fmaxf(s, -hA[i]), hA[i]);
-      t = fminf(fmaxf(t, -hB[j]), hB[j]);
-      float pt[3], nrm[3] = {-Lv[0], -Lv[1], -Lv[2]};
-      for (int k = 0; k < 3; ++k) pt[k] = 0.5f * ((PA[k] + s * Ax[i][k]) + (PB[k] + t * Bx[j][k]));
-      if (n < kCand) put_candidate(cand, n, pt, nrm, ev, a, b);
-      else st |= 8u;
-      added = 1;
+    }
+    return n;
+  }
+  const int i = (ei - 6) / 3, j = (ei - 6) % 3;
+  float Lv[3] = {Le[0], Le[1], Le[2]};
+  if (dot3(D, Lv) < 0.f) { Lv[0] = -Lv[0]; Lv[1] = -Lv[1]; Lv[2] = -Lv[2]; }
+  float PA[3], PB[3];
+  for (int k = 0; k < 3; ++k) { PA[k] = sm.c[k][a]; PB[k] = sm.c[k][b]; }
+  for (int k = 0; k < 3; ++k) {
+    if (k != i) {
+      const float sA = dot3(Ax[k], Lv) >= 0.f ? hA[k] : -hA[k];
+      for (int t = 0; t < 3; ++t) PA[t] += sA * Ax[k][t];
+    }
+    if (k != j) {
+      const float sB = dot3(Bx[k], Lv) >= 0.f ? hB[k] : -hB[k];
+      for (int t = 0; t < 3; ++t) PB[t] -= sB * Bx[k][t];
     }
   }
-  st |= __shfl_sync(kFull, st, 0);
-  added = __shfl_sync(kFull, added, 0);
-  __syncwarp();
-  return n + added;
+  const float wv[3] = {PA[0] - PB[0], PA[1] - PB[1], PA[2] - PB[2]};
+  const float bb = dot3(Ax[i], Bx[j]);
+  const float dd2 = dot3(Ax[i], wv);
+  const float ee = dot3(Bx[j], wv);
+  const float den = 1.f - bb * bb;
+  float s = (bb * ee - dd2) / den;
+  float t = (ee - bb * dd2) / den;
+  s = fminf(fmaxf(s, -hA[i]), hA[i]);
+  t = fminf(fmaxf(t, -hB[j]), hB[j]);
+  for (int k = 0; k < 3; ++k) out[k] = 0.5f * ((PA[k] + s * Ax[i][k]) + (PB[k] + t * Bx[j][k]));
+  out[3] = -Lv[0]; out[4] = -Lv[1]; out[5] = -Lv[2];
+  out[6] = ebest;
+  out[7] = __int_as_float(ab);
+  return 1;
 }
 
 // Duff et al. 2017 ("Building an Orthonormal Basis, Revisited"), JCGT 6(1)
@@ -366,11 +377,11 @@ __device__ __forceinline__ void tangent_basis(const float* n, float* t1, float* 
 }
 
 struct Counters {
-  unsigned long long contacts, narrow, broad, steps;
+  unsigned long long contacts, narrow, broad, steps, cycles;
 };
 
 template <int WPB>
-__global__ void __launch_bounds__(WPB * 32)
+__global__ void __launch_bounds__(WPB * 32, 16 / WPB)
 step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4* __restrict__ meta,
             const uint16_t* __restrict__ pairs, float* __restrict__ qg, float* __restrict__ vg,
             float* __restrict__ sg, unsigned* __restrict__ status, Counters* __restrict__ counters,
@@ -388,23 +399,10 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   const bool body = lane < nb;
   const bool hinge = lane >= 1 && lane < nb;
 
-  // ---- static model, lane = body
-  const float* F = mf + (size_t)var * NF * 32;
+  // static model: [field][body slot] in global memory (L1/L2 resident), read
+  // where it is used; only the topology lives in registers
+  const float* __restrict__ F = mf + (size_t)var * NF * 32;
   const int* IM = mi + (size_t)var * NI * 32;
-  float Rf[9], pf[3], cm[3], mass, Id[3], wint, wcpl;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Rf[k] = F[(F_RFIX + k) * 32 + lane];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    pf[k] = F[(F_PFIX + k) * 32 + lane];
-    cm[k] = F[(F_COM + k) * 32 + lane];
-    Id[k] = F[(F_ID + k) * 32 + lane];
-    sm.half[k][lane] = F[(F_HALF + k) * 32 + lane];
-  }
-  mass = F[F_MASS * 32 + lane];
-  wint = F[F_WINT * 32 + lane];
-  wcpl = F[F_WCPL * 32 + lane];
-  sm.rad[lane] = F[F_RAD * 32 + lane];
   const int parent = body ? IM[I_PARENT * 32 + lane] : -1;
   const int axis = IM[I_AXIS * 32 + lane];
   const unsigned childm = (unsigned)IM[I_CHILD * 32 + lane];
@@ -412,6 +410,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   sm.parent[lane] = parent;
   sm.path[lane] = (unsigned)IM[I_PATH * 32 + lane];
   const int par0 = parent > 0 ? parent : 0;
+  auto fld = [&](int f) { return __ldg(F + f * 32 + lane); };
 
   // ---- state
   float* qv = qg + (size_t)var * 32;
@@ -424,12 +423,26 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   float xo = hinge ? sv[2 * (lane - 1)] : 0.f;
   float yo = hinge ? sv[2 * (lane - 1) + 1] : 0.f;
   unsigned st = status[var];
-  unsigned long long n_contacts = 0, n_narrow = 0, n_broad = 0, n_steps = 0;
+  unsigned n_contacts = 0, n_narrow = 0, n_broad = 0, n_steps = 0;
   int nc_last = last_nc[var];
   float vfree_last = 0.f;
+  float lam_a[3] = {0.f, 0.f, 0.f}, lam_b[3] = {0.f, 0.f, 0.f};  // impulses of contacts lane, lane + 32
 
+  const long long t_start = clock64();
+  // per-phase SM cycles (kept on every lane, written by lane 0 at the end):
+  // 0 CPG+FK, 1 inertias+RNEA+CRBA, 2 Cholesky+v_free, 3 ground contacts,
+  // 4 box/box, 5 cap, 6 contact rows, 7 Gauss-Seidel, 8 integration
+  unsigned long long ph[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long tph = clock64();
+#define B3_PHASE(i)                                   \
+  do {                                                \
+    const long long t_ = clock64();                   \
+    ph[i] += (unsigned long long)(t_ - tph);          \
+    tph = t_;                                         \
+  } while (0)
   float* cand = scratch + (size_t)var * kScratchFloats;
-  float* Yg = cand + (size_t)kCand * kCandW;
+  float* Yg = cand + kYOffset;
+  float* cstg = cand + kCstOffset;
   __syncwarp();
 
   for (int step = 0; step < nsteps; ++step) {
@@ -440,6 +453,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     float xn = xo, yn = yo, tau_b = 0.f;
     const float thd_b = shf(vd, (5 + lane) & 31);
     if (P.actuate) {
+      const float wint = fld(F_WINT), wcpl = fld(F_WCPL);
       sm.acc[0][lane] = (hinge && parent >= 1) ? wcpl * xo : 0.f;
       __syncwarp();
       float dx = wint * yo, dy = -wint * xo;
@@ -462,44 +476,43 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     float R0[9];
     quat_to_R(qw, qx, qy, qz, R0);
     float R[9], r[3] = {0.f, 0.f, 0.f};
-    float Rl[9];
+    float sth, cth;
+    sincosf(theta, &sth, &cth);
     {
-      float sth, cth;
-      sincosf(theta, &sth, &cth);
+      float Rl[9];
       const int k = axis, i = (axis + 1) % 3, j = (axis + 2) % 3;
 #pragma unroll
       for (int row = 0; row < 3; ++row) {
-        float fi = Rf[3 * row + i], fj = Rf[3 * row + j];
-        Rl[3 * row + k] = Rf[3 * row + k];
+        const float fi = fld(F_RFIX + 3 * row + i), fj = fld(F_RFIX + 3 * row + j);
+        Rl[3 * row + k] = fld(F_RFIX + 3 * row + k);
         Rl[3 * row + i] = cth * fi + sth * fj;
         Rl[3 * row + j] = -sth * fi + cth * fj;
       }
-    }
+      const float pf0 = fld(F_PFIX), pf1 = fld(F_PFIX + 1), pf2 = fld(F_PFIX + 2);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = R0[k];
-    for (int lvl = 1; lvl <= maxdepth; ++lvl) {
-      float Rp[9], rp[3];
+      for (int k2 = 0; k2 < 9; ++k2) R[k2] = R0[k2];
+      for (int lvl = 1; lvl <= maxdepth; ++lvl) {
+        float Rp[9], rp[3];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) Rp[k] = shf(R[k], par0);
+        for (int k2 = 0; k2 < 9; ++k2) Rp[k2] = shf(R[k2], par0);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) rp[k] = shf(r[k], par0);
-      if (depth == lvl) {
+        for (int k2 = 0; k2 < 3; ++k2) rp[k2] = shf(r[k2], par0);
+        if (depth == lvl) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int b = 0; b < 3; ++b)
-            R[3 * a + b] = Rp[3 * a] * Rl[b] + Rp[3 * a + 1] * Rl[3 + b] + Rp[3 * a + 2] * Rl[6 + b];
+            for (int b = 0; b < 3; ++b)
+              R[3 * a + b] = Rp[3 * a] * Rl[b] + Rp[3 * a + 1] * Rl[3 + b] + Rp[3 * a + 2] * Rl[6 + b];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          r[a] = rp[a] + (Rp[3 * a] * pf[0] + Rp[3 * a + 1] * pf[1] + Rp[3 * a + 2] * pf[2]);
+          for (int a = 0; a < 3; ++a) r[a] = rp[a] + (Rp[3 * a] * pf0 + Rp[3 * a + 1] * pf1 + Rp[3 * a + 2] * pf2);
+        }
       }
     }
     // FP64 height chain for the ground contacts: the third row of R_b and the
     // frame-origin height relative to O.  A contact's push-out speed is
-    // ERP * depth / dt with depths of ~0.1 mm, and FP32 kinematics carries
-    // ~5 nm of rounding in heights, which would move a resting robot's
-    // one-step velocity by ~1e-5; heights are therefore evaluated in FP64
-    // (from the FP32 state), everything else stays FP32.
+    // ERP * depth / dt with depths of ~0.1 mm; heights are evaluated in FP64
+    // (from the FP32 state) so that contact activation is decided in the same
+    // precision as the FP64 reference; everything else stays FP32.
     double hz0, hz1, hz2, hzb = 0.0;
     {
       const double dw = qw, dx = qx, dy = qy, dz = qz;
@@ -509,28 +522,32 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       double sd, cd;
       sincos((double)theta, &sd, &cd);
       const int k = axis, i = (axis + 1) % 3, j = (axis + 2) % 3;
-      double Ld[9];
-#pragma unroll
-      for (int row = 0; row < 3; ++row) {
-        const double fi = Rf[3 * row + i], fj = Rf[3 * row + j];
-        Ld[3 * row + k] = Rf[3 * row + k];
-        Ld[3 * row + i] = cd * fi + sd * fj;
-        Ld[3 * row + j] = -sd * fi + cd * fj;
-      }
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
         const double p0 = __shfl_sync(kFull, hz0, par0), p1 = __shfl_sync(kFull, hz1, par0);
         const double p2 = __shfl_sync(kFull, hz2, par0), pb = __shfl_sync(kFull, hzb, par0);
         if (depth == lvl) {
-          hz0 = p0 * Ld[0] + p1 * Ld[3] + p2 * Ld[6];
-          hz1 = p0 * Ld[1] + p1 * Ld[4] + p2 * Ld[7];
-          hz2 = p0 * Ld[2] + p1 * Ld[5] + p2 * Ld[8];
-          hzb = pb + (p0 * (double)pf[0] + p1 * (double)pf[1] + p2 * (double)pf[2]);
+          // (third row of R_parent) x R_fix, then the hinge rotation mixes columns i, j
+          double t[3];
+#pragma unroll
+          for (int col = 0; col < 3; ++col)
+            t[col] = p0 * (double)fld(F_RFIX + col) + p1 * (double)fld(F_RFIX + 3 + col) +
+                     p2 * (double)fld(F_RFIX + 6 + col);
+          const double ti = t[i], tj = t[j];
+          double out[3];
+          out[k] = t[k];
+          out[i] = cd * ti + sd * tj;
+          out[j] = -sd * ti + cd * tj;
+          hz0 = out[0]; hz1 = out[1]; hz2 = out[2];
+          hzb = pb + (p0 * (double)fld(F_PFIX) + p1 * (double)fld(F_PFIX + 1) + p2 * (double)fld(F_PFIX + 2));
         }
       }
     }
     float cb[3];
+    {
+      const float c0 = fld(F_COM), c1 = fld(F_COM + 1), c2 = fld(F_COM + 2);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cb[a] = r[a] + (R[3 * a] * cm[0] + R[3 * a + 1] * cm[1] + R[3 * a + 2] * cm[2]);
+      for (int a = 0; a < 3; ++a) cb[a] = r[a] + (R[3 * a] * c0 + R[3 * a + 1] * c1 + R[3 * a + 2] * c2);
+    }
     float Sb[6];
     Sb[0] = R[axis]; Sb[1] = R[3 + axis]; Sb[2] = R[6 + axis];
     cross3(r, Sb, Sb + 3);
@@ -550,53 +567,55 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int k = 0; k < 6; ++k) sm.S[k][lane] = col[k];
     }
 
+    B3_PHASE(0);
     // ---------------- 3. spatial inertias and RNEA bias forces
-    float I[10];
     {
-      float Iw[6];  // xx yy zz xy xz yz of R diag(Id) R^T
-      Iw[0] = R[0] * R[0] * Id[0] + R[1] * R[1] * Id[1] + R[2] * R[2] * Id[2];
-      Iw[1] = R[3] * R[3] * Id[0] + R[4] * R[4] * Id[1] + R[5] * R[5] * Id[2];
-      Iw[2] = R[6] * R[6] * Id[0] + R[7] * R[7] * Id[1] + R[8] * R[8] * Id[2];
-      Iw[3] = R[0] * R[3] * Id[0] + R[1] * R[4] * Id[1] + R[2] * R[5] * Id[2];
-      Iw[4] = R[0] * R[6] * Id[0] + R[1] * R[7] * Id[1] + R[2] * R[8] * Id[2];
-      Iw[5] = R[3] * R[6] * Id[0] + R[4] * R[7] * Id[1] + R[5] * R[8] * Id[2];
-      float cc = cb[0] * cb[0] + cb[1] * cb[1] + cb[2] * cb[2];
-      I[0] = mass;
-      I[1] = mass * cb[0]; I[2] = mass * cb[1]; I[3] = mass * cb[2];
-      I[4] = Iw[0] + mass * (cc - cb[0] * cb[0]);
-      I[5] = Iw[1] + mass * (cc - cb[1] * cb[1]);
-      I[6] = Iw[2] + mass * (cc - cb[2] * cb[2]);
-      I[7] = Iw[3] - mass * cb[0] * cb[1];
-      I[8] = Iw[4] - mass * cb[0] * cb[2];
-      I[9] = Iw[5] - mass * cb[1] * cb[2];
-    }
-    const float vlx = shf(vd, 0), vly = shf(vd, 1), vlz = shf(vd, 2);
-    const float wbx = shf(vd, 3), wby = shf(vd, 4), wbz = shf(vd, 5);
-    float vb[6], ab[6];
-    {
-      float om[3] = {R0[0] * wbx + R0[1] * wby + R0[2] * wbz, R0[3] * wbx + R0[4] * wby + R0[5] * wbz,
-                     R0[6] * wbx + R0[7] * wby + R0[8] * wbz};
-      float vl[3] = {vlx, vly, vlz};
-      float vxw[3];
-      cross3(vl, om, vxw);
-      vb[0] = om[0]; vb[1] = om[1]; vb[2] = om[2]; vb[3] = vlx; vb[4] = vly; vb[5] = vlz;
-      ab[0] = 0.f; ab[1] = 0.f; ab[2] = 0.f;
-      ab[3] = vxw[0] - P.gx; ab[4] = vxw[1] - P.gy; ab[5] = vxw[2] - P.gz;
-    }
-    for (int lvl = 1; lvl <= maxdepth; ++lvl) {
-      float vp[6], ap[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) { vp[k] = shf(vb[k], par0); ap[k] = shf(ab[k], par0); }
-      if (depth == lvl) {
-        float Sq[6], cr[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) { Sq[k] = Sb[k] * thd_b; vb[k] = vp[k] + Sq[k]; }
-        crm(vb, Sq, cr);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) ab[k] = ap[k] + cr[k];
+      float I[10];
+      {
+        const float mass = fld(F_MASS), i0 = fld(F_ID), i1 = fld(F_ID + 1), i2 = fld(F_ID + 2);
+        float Iw[6];  // xx yy zz xy xz yz of R diag(Id) R^T
+        Iw[0] = R[0] * R[0] * i0 + R[1] * R[1] * i1 + R[2] * R[2] * i2;
+        Iw[1] = R[3] * R[3] * i0 + R[4] * R[4] * i1 + R[5] * R[5] * i2;
+        Iw[2] = R[6] * R[6] * i0 + R[7] * R[7] * i1 + R[8] * R[8] * i2;
+        Iw[3] = R[0] * R[3] * i0 + R[1] * R[4] * i1 + R[2] * R[5] * i2;
+        Iw[4] = R[0] * R[6] * i0 + R[1] * R[7] * i1 + R[2] * R[8] * i2;
+        Iw[5] = R[3] * R[6] * i0 + R[4] * R[7] * i1 + R[5] * R[8] * i2;
+        const float cc = cb[0] * cb[0] + cb[1] * cb[1] + cb[2] * cb[2];
+        I[0] = mass;
+        I[1] = mass * cb[0]; I[2] = mass * cb[1]; I[3] = mass * cb[2];
+        I[4] = Iw[0] + mass * (cc - cb[0] * cb[0]);
+        I[5] = Iw[1] + mass * (cc - cb[1] * cb[1]);
+        I[6] = Iw[2] + mass * (cc - cb[2] * cb[2]);
+        I[7] = Iw[3] - mass * cb[0] * cb[1];
+        I[8] = Iw[4] - mass * cb[0] * cb[2];
+        I[9] = Iw[5] - mass * cb[1] * cb[2];
       }
-    }
-    {
+      const float vlx = shf(vd, 0), vly = shf(vd, 1), vlz = shf(vd, 2);
+      const float wbx = shf(vd, 3), wby = shf(vd, 4), wbz = shf(vd, 5);
+      float vb[6], ab[6];
+      {
+        float om[3] = {R0[0] * wbx + R0[1] * wby + R0[2] * wbz, R0[3] * wbx + R0[4] * wby + R0[5] * wbz,
+                       R0[6] * wbx + R0[7] * wby + R0[8] * wbz};
+        float vl[3] = {vlx, vly, vlz};
+        float vxw[3];
+        cross3(vl, om, vxw);
+        vb[0] = om[0]; vb[1] = om[1]; vb[2] = om[2]; vb[3] = vlx; vb[4] = vly; vb[5] = vlz;
+        ab[0] = 0.f; ab[1] = 0.f; ab[2] = 0.f;
+        ab[3] = vxw[0] - P.gx; ab[4] = vxw[1] - P.gy; ab[5] = vxw[2] - P.gz;
+      }
+      for (int lvl = 1; lvl <= maxdepth; ++lvl) {
+        float vp[6], ap[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { vp[k] = shf(vb[k], par0); ap[k] = shf(ab[k], par0); }
+        if (depth == lvl) {
+          float Sq[6], cr[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) { Sq[k] = Sb[k] * thd_b; vb[k] = vp[k] + Sq[k]; }
+          crm(vb, Sq, cr);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) ab[k] = ap[k] + cr[k];
+        }
+      }
       float Ia[6], Iv[6], x[6];
       inertia_apply(I, ab, Ia);
       inertia_apply(I, vb, Iv);
@@ -630,8 +649,9 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
     }
 
-    // ---------------- 4. CRBA mass matrix (lower triangle, row stride kLs)
-    for (int j = 0; j <= lane && lane < nv; ++j) sm.M[lane * kLs + j] = 0.f;
+    // ---------------- 4. CRBA mass matrix (packed lower triangle)
+    if (lane < nv)
+      for (int j = 0; j <= lane; ++j) sm.M[tri(lane) + j] = 0.f;
     __syncwarp();
     if (hinge) {
       float Ic[10], Fv[6];
@@ -639,18 +659,18 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int k = 0; k < 10; ++k) Ic[k] = sm.acc[6 + k][lane];
       inertia_apply(Ic, Sb, Fv);
       const int i = 5 + lane;
-      sm.M[i * kLs + i] = Sb[0] * Fv[0] + Sb[1] * Fv[1] + Sb[2] * Fv[2] + Sb[3] * Fv[3] + Sb[4] * Fv[4] +
-                          Sb[5] * Fv[5] + P.armature;
+      const int ti = tri(i);
+      sm.M[ti + i] = Sb[0] * Fv[0] + Sb[1] * Fv[1] + Sb[2] * Fv[2] + Sb[3] * Fv[3] + Sb[4] * Fv[4] + Sb[5] * Fv[5] +
+                     P.armature;
       for (int j = parent; j > 0; j = sm.parent[j]) {
         const int jj = 5 + j;
-        sm.M[i * kLs + jj] = sm.S[0][jj] * Fv[0] + sm.S[1][jj] * Fv[1] + sm.S[2][jj] * Fv[2] +
-                             sm.S[3][jj] * Fv[3] + sm.S[4][jj] * Fv[4] + sm.S[5][jj] * Fv[5];
+        sm.M[ti + jj] = sm.S[0][jj] * Fv[0] + sm.S[1][jj] * Fv[1] + sm.S[2][jj] * Fv[2] + sm.S[3][jj] * Fv[3] +
+                        sm.S[4][jj] * Fv[4] + sm.S[5][jj] * Fv[5];
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) sm.M[i * kLs + k] = Fv[3 + k];
+      for (int k = 0; k < 3; ++k) sm.M[ti + k] = Fv[3 + k];
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        sm.M[i * kLs + 3 + k] = R0[k] * Fv[0] + R0[3 + k] * Fv[1] + R0[6 + k] * Fv[2];
+      for (int k = 0; k < 3; ++k) sm.M[ti + 3 + k] = R0[k] * Fv[0] + R0[3 + k] * Fv[1] + R0[6 + k] * Fv[2];
     }
     if (lane < 6) {
       float Ic[10], Sk[6], Fv[6];
@@ -660,29 +680,33 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int k = 0; k < 6; ++k) Sk[k] = sm.S[k][lane];
       inertia_apply(Ic, Sk, Fv);
       for (int l = lane; l < 6; ++l)
-        sm.M[l * kLs + lane] = sm.S[0][l] * Fv[0] + sm.S[1][l] * Fv[1] + sm.S[2][l] * Fv[2] +
-                               sm.S[3][l] * Fv[3] + sm.S[4][l] * Fv[4] + sm.S[5][l] * Fv[5];
+        sm.M[tri(l) + lane] = sm.S[0][l] * Fv[0] + sm.S[1][l] * Fv[1] + sm.S[2][l] * Fv[2] + sm.S[3][l] * Fv[3] +
+                              sm.S[4][l] * Fv[4] + sm.S[5][l] * Fv[5];
     }
     __syncwarp();
 
+    B3_PHASE(1);
     // ---------------- 5. Cholesky (right-looking, lane = row) and v_free
     bool chol_ok = true;
-    for (int k = 0; k < nv; ++k) {
-      const float dkk = sm.M[k * kLs + k];
-      if (!(dkk > 0.f)) { chol_ok = false; break; }
-      const float d = sqrtf(dkk);
-      const float inv = 1.f / d;
-      float lik = 0.f;
-      if (lane > k && lane < nv) lik = sm.M[lane * kLs + k] * inv;
-      __syncwarp();
-      if (lane == k) { sm.M[k * kLs + k] = d; sm.invd[k] = inv; }
-      if (lane > k && lane < nv) sm.M[lane * kLs + k] = lik;
-      __syncwarp();
-      for (int j = k + 1; j < nv; ++j) {
-        const float ljk = sm.M[j * kLs + k];
-        if (lane >= j && lane < nv) sm.M[lane * kLs + j] -= lik * ljk;
+    {
+      const int tl = tri(lane);
+      for (int k = 0; k < nv; ++k) {
+        const float dkk = sm.M[tri(k) + k];
+        if (!(dkk > 0.f)) { chol_ok = false; break; }
+        const float d = sqrtf(dkk);
+        const float inv = 1.f / d;
+        float lik = 0.f;
+        if (lane > k && lane < nv) lik = sm.M[tl + k] * inv;
+        __syncwarp();
+        if (lane == k) { sm.M[tl + k] = d; sm.invd[k] = inv; }
+        if (lane > k && lane < nv) sm.M[tl + k] = lik;
+        __syncwarp();
+        for (int j = k + 1; j < nv; ++j) {
+          const float ljk = sm.M[tri(j) + k];
+          if (lane >= j && lane < nv) sm.M[tl + j] -= lik * ljk;
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     if (!chol_ok) { st |= 4u; break; }
     float vfree;
@@ -694,49 +718,53 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       vfree_last = sm.vfree[lane];
     }
 
+    B3_PHASE(2);
     // ---------------- 6. contact candidates
-    const float Oz = p0z;
     int ncand = 0;
     if (P.ground) {
       unsigned mask8 = 0;
-      float lv[8][3];
       float zdepth[8];
+      const float h0 = fld(F_HALF), h1 = fld(F_HALF + 1), h2 = fld(F_HALF + 2);
+      const float c0 = fld(F_COM), c1 = fld(F_COM + 1), c2 = fld(F_COM + 2);
       if (body) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-            lv[k][i] = cm[i] + (((k >> i) & 1) ? 1.f : -1.f) * sm.half[i][lane];
-          const double z = (double)Oz + (hzb + (hz0 * (double)lv[k][0] + hz1 * (double)lv[k][1] +
-                                                 hz2 * (double)lv[k][2]));
+          const double l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
+          const double z = (double)p0z + (hzb + (hz0 * l0 + hz1 * l1 + hz2 * l2));
           if (z < 0.0) mask8 |= 1u << k;
           zdepth[k] = (float)(-z);
         }
       }
-      int cnt = __popc(mask8);
+      const int cnt = __popc(mask8);
       int incl = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(kFull, incl, o);
+        const int t = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += t;
       }
       int off = incl - cnt;
       const float up[3] = {0.f, 0.f, 1.f};
-      for (unsigned m = mask8; m; m &= m - 1) {
-        const int k = __ffs(m) - 1;
-        float pr[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          pr[a] = r[a] + (R[3 * a] * lv[k][0] + R[3 * a + 1] * lv[k][1] + R[3 * a + 2] * lv[k][2]);
-        if (off < kCand) put_candidate(cand, off, pr, up, zdepth[k], lane, 255);
-        ++off;
+      for (int k = 0; k < 8; ++k) {
+        if (mask8 & (1u << k)) {
+          const float l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
+          float pr[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) pr[a] = r[a] + (R[3 * a] * l0 + R[3 * a + 1] * l1 + R[3 * a + 2] * l2);
+          if (off < kCand) put_candidate(cand, off, pr, up, zdepth[k], lane, 255);
+          ++off;
+        }
       }
       ncand = shfi(incl, 31);
-      if (ncand > kCand) { st |= 8u; }
+      if (ncand > kCand) st |= 8u;
       ncand = min(ncand, kCand);
     }
     __syncwarp();
+    B3_PHASE(3);
     if (P.box_box) {
+      // lane = pair: broad phase, then the narrow phase of every near pair on
+      // its own lane; contacts are placed in pair order by a warp scan
+      float* stage = cand + kStageOffset + (size_t)lane * 8 * kCandW;
       for (int p0 = 0; p0 < npairs; p0 += 32) {
         const int pi = p0 + lane;
         int a = 0, b = 0;
@@ -746,22 +774,34 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           a = (int)(pr >> 8);
           b = (int)(pr & 0xffu);
           const float dx = sm.c[0][b] - sm.c[0][a], dy = sm.c[1][b] - sm.c[1][a], dz = sm.c[2][b] - sm.c[2][a];
-          const float rr = sm.rad[a] + sm.rad[b];
+          const float rr = __ldg(F + F_RAD * 32 + a) + __ldg(F + F_RAD * 32 + b);
           near = dx * dx + dy * dy + dz * dz <= rr * rr;
         }
         n_broad += (unsigned)max(0, min(32, npairs - p0));
-        unsigned cm_ = __ballot_sync(kFull, near);
-        while (cm_) {
-          const int src = __ffs(cm_) - 1;
-          cm_ &= cm_ - 1;
-          const int aa = shfi(a, src), bb = shfi(b, src);
-          ++n_narrow;
-          ncand = box_box_pair(sm, cand, ncand, aa, bb, lane, st);
+        const unsigned nm = __ballot_sync(kFull, near);
+        if (!nm) continue;
+        n_narrow += (unsigned)__popc(nm);
+        const int cnt = near ? box_box_lane(sm, F, a, b, stage) : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
         }
+        const int off = ncand + incl - cnt;
+        for (int i = 0; i < cnt; ++i) {
+          if (off + i < kCand) {
+#pragma unroll
+            for (int k = 0; k < kCandW; ++k) cand[(size_t)(off + i) * kCandW + k] = stage[i * kCandW + k];
+          }
+        }
+        ncand += shfi(incl, 31);
+        __syncwarp();
       }
       if (ncand > kCand) { st |= 8u; ncand = kCand; }
     }
     __syncwarp();
+    B3_PHASE(4);
     // keep the cap deepest (ties by list order), list order kept: ranks of
     // every candidate first, then an in-order compaction (destination <= source)
     int nc = ncand;
@@ -808,141 +848,160 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     nc_last = nc;
     __syncwarp();
 
-    // ---------------- 7. contact rows: Y = L^-1 J^T and Gauss-Seidel constants (lane = contact)
-    for (int k0 = 0; k0 < nc; k0 += 32) {
-      const int k = k0 + lane;
-      const bool act = k < nc;
-      float pr[3] = {0.f, 0.f, 0.f}, nrm[3] = {0.f, 0.f, 1.f}, depth_k = 0.f;
+    B3_PHASE(5);
+    // ---------------- 7. contact rows: Y_r = L^-1 J_r^T and Gauss-Seidel constants (lane = row)
+    for (int r0 = 0; r0 < 3 * nc; r0 += 32) {
+      const int row = r0 + lane;
+      const bool act = row < 3 * nc;
+      const int k = act ? row / 3 : 0;
+      const int dir = row - 3 * k;
+      float pr[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f}, depth_k = 0.f;
       unsigned pa = 0u, pb = 0u;
       float sroot = 0.f;
       if (act) {
-        const float* row = cand + (size_t)k * kCandW;
-        pr[0] = row[0]; pr[1] = row[1]; pr[2] = row[2];
-        nrm[0] = row[3]; nrm[1] = row[4]; nrm[2] = row[5];
-        depth_k = row[6];
-        const int ab = __float_as_int(row[7]);
+        const float4* rw = reinterpret_cast<const float4*>(cand + (size_t)k * kCandW);
+        const float4 w0 = rw[0], w1 = rw[1];
+        pr[0] = w0.x; pr[1] = w0.y; pr[2] = w0.z;
+        const float nrm[3] = {w0.w, w1.x, w1.y};
+        depth_k = w1.z;
+        const int ab = __float_as_int(w1.w);
         const int a = ab & 0xff, b = (ab >> 8) & 0xff;
         pa = sm.path[a];
         pb = b == 255 ? 0u : sm.path[b];
         sroot = (b == 255) ? 1.f : 0.f;
-      }
-      float t1[3], t2[3];
-      tangent_basis(nrm, t1, t2);
-      float yn[32];
-      float cst[12];
-#pragma unroll 1
-      for (int dir = 0; dir < 3; ++dir) {
-        float d[3];
+        float t1[3], t2[3];
+        tangent_basis(nrm, t1, t2);
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = dir == 0 ? nrm[q] : (dir == 1 ? t1[q] : t2[q]);
-        float wa[3];
-        cross3(pr, d, wa);
-        float y[32];
-        float jv = 0.f;
+      }
+      float wa[3];
+      cross3(pr, d, wa);
+      float y[32];
+      float jv = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float Jj = 0.f;
-          if (j < nv) {
-            float coef;
-            if (j < 6) coef = sroot;
-            else {
-              const int bj = j - 5;
-              coef = (float)((int)((pa >> bj) & 1u) - (int)((pb >> bj) & 1u));
-            }
-            Jj = coef * (sm.S[0][j] * wa[0] + sm.S[1][j] * wa[1] + sm.S[2][j] * wa[2] + sm.S[3][j] * d[0] +
-                         sm.S[4][j] * d[1] + sm.S[5][j] * d[2]);
-            jv += Jj * sm.vfree[j];
+      for (int j = 0; j < 32; ++j) {
+        float Jj = 0.f;
+        if (j < nv) {
+          float coef;
+          if (j < 6) coef = sroot;
+          else {
+            const int bj = j - 5;
+            coef = (float)((int)((pa >> bj) & 1u) - (int)((pb >> bj) & 1u));
           }
-          y[j] = Jj;
+          Jj = coef * (sm.S[0][j] * wa[0] + sm.S[1][j] * wa[1] + sm.S[2][j] * wa[2] + sm.S[3][j] * d[0] +
+                       sm.S[4][j] * d[1] + sm.S[5][j] * d[2]);
+          jv += Jj * sm.vfree[j];
         }
-        // forward substitution y <- L^-1 y, L broadcast from shared memory
+        y[j] = Jj;
+      }
+      // forward substitution y <- L^-1 y, L broadcast from shared memory
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (i < nv) {
-            float t = y[i];
+      for (int i = 0; i < 32; ++i) {
+        if (i < nv) {
+          const int ti = tri(i);
+          float t = y[i];
 #pragma unroll
-            for (int kk = 0; kk < i; ++kk) t -= sm.M[i * kLs + kk] * y[kk];
-            y[i] = t * sm.invd[i];
-          }
+          for (int kk = 0; kk < i; ++kk) t -= sm.M[ti + kk] * y[kk];
+          y[i] = t * sm.invd[i];
         }
-        float aa = 0.f, an = 0.f;
+      }
+      float aa = 0.f;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (i < nv) {
-            aa += y[i] * y[i];
-            if (dir > 0) an += y[i] * yn[i];
-          }
-        }
-        if (act) {
-          float4* dst = reinterpret_cast<float4*>(Yg + (size_t)(3 * k + dir) * 32);
+      for (int i = 0; i < 32; ++i)
+        if (i < nv) aa += y[i] * y[i];
+      if (act) {
+        float4* dst = reinterpret_cast<float4*>(Yg + (size_t)row * 32);
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            dst[i] = make_float4(i * 4 + 0 < nv ? y[i * 4 + 0] : 0.f, i * 4 + 1 < nv ? y[i * 4 + 1] : 0.f,
-                                 i * 4 + 2 < nv ? y[i * 4 + 2] : 0.f, i * 4 + 3 < nv ? y[i * 4 + 3] : 0.f);
-        }
+        for (int i = 0; i < 8; ++i)
+          dst[i] = make_float4(i * 4 + 0 < nv ? y[i * 4 + 0] : 0.f, i * 4 + 1 < nv ? y[i * 4 + 1] : 0.f,
+                               i * 4 + 2 < nv ? y[i * 4 + 2] : 0.f, i * 4 + 3 < nv ? y[i * 4 + 3] : 0.f);
         const float Rr = P.kappa * aa;
         // a row that no dof can move (J = 0) carries no impulse: 1/(A+R) = 0
         const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
-        if (dir == 0) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) yn[i] = y[i];
-          // penetration recovery speed, capped (ODE's maximum correcting velocity)
-          cst[0] = jv - fminf(P.erp * depth_k / dt, P.max_correct_vel);
-          cst[1] = inv;
-          cst[2] = Rr;
-        } else {
-          cst[3 * dir + 0] = jv;
-          cst[3 * dir + 1] = inv;
-          cst[3 * dir + 2] = Rr;
-          cst[8 + dir] = an;
-        }
-      }
-      if (act) {
-#pragma unroll
-        for (int i = 0; i < 11; ++i) sm.cst[k][i] = cst[i];
-        sm.lam[k][0] = 0.f; sm.lam[k][1] = 0.f; sm.lam[k][2] = 0.f;
+        // penetration recovery speed, capped (ODE's maximum correcting velocity)
+        const float bias = dir == 0 ? jv - fminf(P.erp * depth_k / dt, P.max_correct_vel) : jv;
+        float* cs = cstg + (size_t)k * 12 + 3 * dir;
+        cs[0] = bias;
+        cs[1] = inv;
+        cs[2] = Rr;
       }
     }
     __syncwarp();
-
-    // ---------------- 8. soft projected Gauss-Seidel (lane = dof, u = L^T (v - v_free))
-    float u = 0.f;
-    for (int it = 0; it < P.iters; ++it) {
-      for (int k = 0; k < nc; ++k) {
-        const float* Yk = Yg + (size_t)(3 * k) * 32;
-        const float y0 = Yk[lane], y1 = Yk[32 + lane], y2 = Yk[64 + lane];
-        float s0 = y0 * u, s1 = y1 * u, s2 = y2 * u;
+    // tangent/normal coupling A_tn = Y_t . Y_n of each contact (lane = contact)
+    for (int k0 = 0; k0 < nc; k0 += 32) {
+      const int k = k0 + lane;
+      if (k < nc) {
+        const float4* yn = reinterpret_cast<const float4*>(Yg + (size_t)(3 * k) * 32);
+        const float4* y1 = yn + 8;
+        const float4* y2 = yn + 16;
+        float a1 = 0.f, a2 = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          s0 += __shfl_xor_sync(kFull, s0, o);
-          s1 += __shfl_xor_sync(kFull, s1, o);
-          s2 += __shfl_xor_sync(kFull, s2, o);
+        for (int i = 0; i < 8; ++i) {
+          const float4 n4 = yn[i], p4 = y1[i], q4 = y2[i];
+          a1 += p4.x * n4.x + p4.y * n4.y + p4.z * n4.z + p4.w * n4.w;
+          a2 += q4.x * n4.x + q4.y * n4.y + q4.z * n4.z + q4.w * n4.w;
         }
-        const float* cs = sm.cst[k];
-        const float ln = sm.lam[k][0], l1 = sm.lam[k][1], l2 = sm.lam[k][2];
-        const float gn = s0 + cs[0] + cs[2] * ln;
-        const float lnn = fmaxf(0.f, ln - gn * cs[1]);
-        const float dn = lnn - ln;
-        const float g1 = s1 + cs[9] * dn + cs[3] + cs[5] * l1;
-        const float g2 = s2 + cs[10] * dn + cs[6] + cs[8] * l2;
-        float l1t = l1 - g1 * cs[4];
-        float l2t = l2 - g2 * cs[7];
-        const float lim = P.mu * lnn;
-        const float nt2 = l1t * l1t + l2t * l2t;
-        if (nt2 > lim * lim) {
-          const float sc = lim / sqrtf(nt2);
-          l1t *= sc;
-          l2t *= sc;
+        float* cs = cstg + (size_t)k * 12;
+        cs[9] = a1;
+        cs[10] = a2;
+        cs[11] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) { lam_a[t] = 0.f; lam_b[t] = 0.f; }
+    __syncwarp();
+
+    B3_PHASE(6);
+    // ---------------- 8. soft projected Gauss-Seidel (lane = dof, u = L^T (v - v_free));
+    // the impulses of contact k live in lane k & 31 (slot k >> 5)
+    float u = 0.f;
+    if (nc > 0) {
+      float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
+      const float4* c4 = reinterpret_cast<const float4*>(cstg);
+      float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
+      for (int it = 0; it < P.iters; ++it) {
+        for (int k = 0; k < nc; ++k) {
+          // prefetch the next contact's rows and constants
+          const int kn = (k + 1 < nc) ? k + 1 : 0;
+          const float* Yn = Yg + (size_t)(3 * kn) * 32;
+          const float ny0 = Yn[lane], ny1 = Yn[32 + lane], ny2 = Yn[64 + lane];
+          const float4 na = c4[3 * kn], nb4 = c4[3 * kn + 1], nc4 = c4[3 * kn + 2];
+          float s0 = y0 * u, s1 = y1 * u, s2 = y2 * u;
+          warp_sum3(s0, s1, s2, lane);
+          const int src = k & 31;
+          const bool hi = k >= 32;
+          const float ln = shf(hi ? lam_b[0] : lam_a[0], src);
+          const float l1 = shf(hi ? lam_b[1] : lam_a[1], src);
+          const float l2 = shf(hi ? lam_b[2] : lam_a[2], src);
+          // constants: (b_n, inv_n, R_n, b_t1), (inv_t1, R_t1, b_t2, inv_t2), (R_t2, A_t1n, A_t2n, 0)
+          const float gn = s0 + ca.x + ca.z * ln;
+          const float lnn = fmaxf(0.f, ln - gn * ca.y);
+          const float dn = lnn - ln;
+          const float g1 = s1 + cc4.y * dn + ca.w + cb4.y * l1;
+          const float g2 = s2 + cc4.z * dn + cb4.z + cc4.x * l2;
+          float l1t = l1 - g1 * cb4.x;
+          float l2t = l2 - g2 * cb4.w;
+          const float lim = P.mu * lnn;
+          const float nt2 = l1t * l1t + l2t * l2t;
+          if (nt2 > lim * lim) {
+            const float sc = lim * rsqrtf(nt2);
+            l1t *= sc;
+            l2t *= sc;
+          }
+          u += y0 * dn + y1 * (l1t - l1) + y2 * (l2t - l2);
+          if (lane == src) {
+            if (hi) { lam_b[0] = lnn; lam_b[1] = l1t; lam_b[2] = l2t; }
+            else { lam_a[0] = lnn; lam_a[1] = l1t; lam_a[2] = l2t; }
+          }
+          y0 = ny0; y1 = ny1; y2 = ny2;
+          ca = na; cb4 = nb4; cc4 = nc4;
         }
-        u += y0 * dn + y1 * (l1t - l1) + y2 * (l2t - l2);
-        __syncwarp();
-        if (lane == 0) { sm.lam[k][0] = lnn; sm.lam[k][1] = l1t; sm.lam[k][2] = l2t; }
-        __syncwarp();
       }
     }
     float vplus = vfree + upper_solve(sm, u, nv, lane);
     if (lane >= nv) vplus = 0.f;
 
+    B3_PHASE(7);
     // ---------------- 9. semi-implicit Euler
     const float vx = shf(vplus, 0), vy = shf(vplus, 1), vz = shf(vplus, 2);
     const float ox = shf(vplus, 3), oy = shf(vplus, 4), oz = shf(vplus, 5);
@@ -975,7 +1034,9 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     vd = vplus;
     xo = xn; yo = yn;
     ++n_steps;
+    B3_PHASE(8);
   }
+#undef B3_PHASE
 
   // ---- write back
   __syncwarp();
@@ -989,6 +1050,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     c.narrow += n_narrow;
     c.broad += n_broad;
     c.steps += n_steps;
+    c.cycles += (unsigned long long)(clock64() - t_start);
     counters[var] = c;
   }
   if (hinge) {
@@ -1000,10 +1062,24 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   // solver detail of the last step (inspection only)
   float* dbg = scratch + (size_t)var * kScratchFloats + kDbgOffset;
   dbg[lane] = vfree_last;
-  for (int k = lane; k < nc_last && n_steps > 0; k += 32) {
-    dbg[32 + 4 * k] = sm.lam[k][0];
-    dbg[32 + 4 * k + 1] = sm.lam[k][1];
-    dbg[32 + 4 * k + 2] = sm.lam[k][2];
+  if (lane == 31) dbg[31] = n_steps > 0 ? (float)(clock64() - t_start) / (float)n_steps : 0.f;
+  if (lane < kPhases) {
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int i = 0; i < kPhases; ++i) mine = (lane == i) ? ph[i] : mine;
+    dbg[32 + 4 * kCapMax + lane] = n_steps > 0 ? (float)mine / (float)n_steps : 0.f;
+  }
+  if (n_steps > 0) {
+    if (lane < nc_last) {
+      dbg[32 + 4 * lane] = lam_a[0];
+      dbg[32 + 4 * lane + 1] = lam_a[1];
+      dbg[32 + 4 * lane + 2] = lam_a[2];
+    }
+    if (lane + 32 < nc_last) {
+      dbg[32 + 4 * (lane + 32)] = lam_b[0];
+      dbg[32 + 4 * (lane + 32) + 1] = lam_b[1];
+      dbg[32 + 4 * (lane + 32) + 2] = lam_b[2];
+    }
   }
 }
 

@@ -59,7 +59,7 @@ class DevicePopulation(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("contacts", C.c_double), ("narrow_pairs", C.c_double),
-                ("broad_pairs", C.c_double), ("variant_steps", C.c_double)]
+                ("broad_pairs", C.c_double), ("variant_steps", C.c_double), ("sm_cycles", C.c_double)]
 
 
 DEFAULTS = dict(dt=0.002, gravity=(0.0, 0.0, -9.81), pgs_iters=30, soft_tau=0.02, soft_zeta=1.0,
@@ -93,7 +93,7 @@ def lib():
         L.sim_autotune.argtypes = [vp, C.c_int32]
         L.sim_counters_read.argtypes = [vp, P(Counters)]
         L.sim_debug_contacts.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, P(C.c_int32)]
-        L.sim_debug_solver.argtypes = [vp, C.c_int32, vp, vp, P(C.c_int32)]
+        L.sim_debug_solver.argtypes = [vp, C.c_int32, vp, vp, P(C.c_int32), vp]
         L.sim_step_n_noalloc.argtypes = [P(SimConfig), P(DevicePopulation), C.c_int32]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
@@ -243,7 +243,7 @@ class Sim:
         c = Counters()
         self._check(lib().sim_counters_read(self.h, C.byref(c)), "sim_counters_read")
         return dict(contacts=c.contacts, narrow_pairs=c.narrow_pairs, broad_pairs=c.broad_pairs,
-                    variant_steps=c.variant_steps)
+                    variant_steps=c.variant_steps, sm_cycles=c.sm_cycles)
 
     def debug_contacts(self, i: int, max_contacts: int = 64):
         rows = np.zeros((max_contacts, 8), np.float32)
@@ -259,5 +259,8 @@ class Sim:
         vfree = np.zeros(SIM_VW, np.float32)
         lam = np.zeros(3 * SIM_MAX_CONTACT_CAP, np.float32)
         n = C.c_int32(0)
-        self._check(lib().sim_debug_solver(self.h, i, _ptr(vfree), _ptr(lam), C.byref(n)), "sim_debug_solver")
-        return dict(vfree=vfree, lam=lam[:3 * n.value].reshape(-1, 3), n=n.value)
+        cyc = np.zeros(11, np.float32)
+        self._check(lib().sim_debug_solver(self.h, i, _ptr(vfree), _ptr(lam), C.byref(n), _ptr(cyc)),
+                    "sim_debug_solver")
+        return dict(vfree=vfree, lam=lam[:3 * n.value].reshape(-1, 3), n=n.value,
+                    cycles_per_step=float(cyc[0]), phase_cycles=cyc[1:10].copy())
