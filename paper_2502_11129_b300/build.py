@@ -19,7 +19,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 LIBS = {
-    "libb3sim.so": (["b3sim.cu"], ["step_kernel.cuh"]),
+    "libb3sim.so": (["b3sim.cu"], ["step_kernel.cuh"], "b3sim.h"),
+    "libb3sur.so": (["b3sur.cu"], [], "b3sur.h"),
 }
 
 
@@ -32,10 +33,10 @@ def _stale(out, srcs):
 
 def build(force: bool = False, verbose: bool = False) -> list[str]:
     built = []
-    for lib, (srcs, deps) in LIBS.items():
+    for lib, (srcs, deps, header) in LIBS.items():
         out = os.path.join(HERE, lib)
         paths = [os.path.join(CSRC, s) for s in srcs]
-        dep_paths = paths + [os.path.join(CSRC, d) for d in deps] + [os.path.join(INCLUDE, "b3sim.h")]
+        dep_paths = paths + [os.path.join(CSRC, d) for d in deps] + [os.path.join(INCLUDE, header)]
         if not force and not _stale(out, dep_paths):
             continue
         cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",

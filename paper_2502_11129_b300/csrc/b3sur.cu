@@ -1,0 +1,882 @@
+// b3sur.cu -- learned fitness surrogate: BF16 MLP 128 -> 256 -> 256 -> 1 on
+// tensor cores (mma.sync m16n8k16, FP32 accumulate), Adam on FP32 master
+// weights, GPU genotype encoding and top-k selection.
+//
+// Dense layers run through one strided GEMM kernel C(m, n) = sum_k A(m, k)
+// B(n, k) whose epilogue is fused with the layer's bias + ReLU (forward) or
+// the ReLU mask (backward); the same kernel computes the weight gradients by
+// reducing over the batch (strided operands instead of transposed copies).
+// Weights and inputs are BF16; activations and backward operands are carried
+// as BF16 pairs (value = hi + lo, both BF16) and the GEMMs run over both
+// parts, so only the weights and inputs are rounded to 8 mantissa bits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "b3sur.h"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int IN = SUR_IN_DIM;
+constexpr int HID = SUR_HIDDEN;
+constexpr int NP = SUR_NPARAMS;
+constexpr int OW1 = 0;
+constexpr int OB1 = OW1 + HID * IN;
+constexpr int OW2 = OB1 + HID;
+constexpr int OB2 = OW2 + HID * HID;
+constexpr int OW3 = OB2 + HID;
+constexpr int OB3 = OW3 + HID;
+
+enum Epi { EPI_F32 = 0, EPI_BIAS_RELU_BF16 = 1, EPI_MASK_BF16_F32 = 2, EPI_F32_ADD = 3 };
+
+struct GemmArgs {
+  int M, N, K;
+  const bf16* A;
+  long lam, lak;  // A(m, k) = A[m * lam + k * lak]
+  const bf16* B;
+  long lbn, lbk;  // B(n, k) = B[n * lbn + k * lbk]
+  float* Cf;
+  bf16* Cb;
+  bf16* Cb_lo;  // EPI_MASK_BF16_F32: remainder v - bf16(v) as BF16
+  long ldc;
+  const float* bias;
+  const bf16* mask;  // multiply by (mask(m, n) > 0)
+  long ldmask;
+  int epi;
+};
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// 64 x 64 block tile, K step 32, 4 warps of 32 x 32 (2 x 4 MMA tiles each)
+__global__ void __launch_bounds__(128) gemm_bf16(GemmArgs g) {
+  __shared__ __align__(16) bf16 As[64][40];
+  __shared__ __align__(16) bf16 Bs[64][40];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int gid = lane >> 2, tig = lane & 3;
+  const bf16 zero = __float2bfloat16(0.f);
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += 32) {
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+      const int e = tid + 128 * j;
+      int mm, kk;
+      if (g.lak == 1) { mm = e >> 5; kk = e & 31; } else { kk = e >> 6; mm = e & 63; }
+      const int m = m0 + mm, k = k0 + kk;
+      As[mm][kk] = (m < g.M && k < g.K) ? g.A[(long)m * g.lam + (long)k * g.lak] : zero;
+      int nn, kb;
+      if (g.lbk == 1) { nn = e >> 5; kb = e & 31; } else { kb = e >> 6; nn = e & 63; }
+      const int n = n0 + nn, kq = k0 + kb;
+      Bs[nn][kb] = (n < g.N && kq < g.K) ? g.B[(long)n * g.lbn + (long)kq * g.lbk] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int r = wm + mi * 16 + gid;
+        af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
+        af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
+        af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
+        af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int c = wn + ni * 8 + gid;
+        bfr[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2]);
+        bfr[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2 + 8]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = m0 + wm + mi * 16 + gid + 8 * (i >> 1);
+        const int col = n0 + wn + ni * 8 + tig * 2 + (i & 1);
+        if (row >= g.M || col >= g.N) continue;
+        float v = acc[mi][ni][i];
+        const long o = (long)row * g.ldc + col;
+        if (g.epi == EPI_F32) {
+          g.Cf[o] = v;
+        } else if (g.epi == EPI_F32_ADD) {
+          g.Cf[o] += v;
+        } else if (g.epi == EPI_BIAS_RELU_BF16) {
+          v = fmaxf(v + g.bias[col], 0.f);
+          const bf16 hi = __float2bfloat16(v);
+          g.Cb[o] = hi;
+          g.Cb_lo[o] = __float2bfloat16(v - __bfloat162float(hi));
+        } else {
+          const bool on = __bfloat162float(g.mask[(long)row * g.ldmask + col]) > 0.f;
+          v = on ? v : 0.f;
+          const bf16 hi = __float2bfloat16(v);
+          g.Cb[o] = hi;
+          g.Cb_lo[o] = __float2bfloat16(v - __bfloat162float(hi));
+          g.Cf[o] = v;
+        }
+      }
+}
+
+// h = relu(z + b) as FP32 and as a BF16 pair (hi, lo)
+__global__ void bias_relu_split(const float* __restrict__ z, const float* __restrict__ b, int n, float* hf, bf16* hi_out,
+                                bf16* lo_out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)n * HID) return;
+  const float v = fmaxf(z[i] + b[i % HID], 0.f);
+  hf[i] = v;
+  const bf16 hi = __float2bfloat16(v);
+  hi_out[i] = hi;
+  lo_out[i] = __float2bfloat16(v - __bfloat162float(hi));
+}
+
+// y[m] = sum_j H2[m, j] W3[j] + b3 (warp per row)
+__global__ void out_layer(const float* __restrict__ H2, const bf16* __restrict__ W3, const float* __restrict__ b3,
+                          int n, float* y) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float s = 0.f;
+  for (int j = lane; j < HID; j += 32) s += H2[(long)row * HID + j] * __bfloat162float(W3[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s + b3[0];
+}
+
+// dy = 2 (y - t) / n, per-block partial sums of (y - t)^2
+__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, int n, float* dy, float* part) {
+  __shared__ float red[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float e = 0.f;
+  if (i < n) {
+    const float d = y[i] - t[i];
+    dy[i] = 2.f * d / (float)n;
+    e = d * d;
+  }
+  red[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// dZ2 = dy * W3 * (H2 > 0) as a BF16 pair (hi, lo = remainder) for the next GEMMs
+__global__ void dz2_kernel(const float* __restrict__ dy, const bf16* __restrict__ W3, const float* __restrict__ H2,
+                           int n, bf16* dZ2, bf16* dZ2lo) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)n * HID) return;
+  const int m = (int)(i / HID), j = (int)(i % HID);
+  const float on = H2[i] > 0.f ? 1.f : 0.f;
+  const float v = dy[m] * __bfloat162float(W3[j]) * on;
+  const bf16 hi = __float2bfloat16(v);
+  dZ2[i] = hi;
+  dZ2lo[i] = __float2bfloat16(v - __bfloat162float(hi));
+}
+
+// dZ1 = dH1 * (H1 > 0): FP32 in place and as a BF16 pair (hi, lo)
+__global__ void relu_mask_split(float* __restrict__ dz, const bf16* __restrict__ H1, const bf16* __restrict__ H1lo,
+                                int n, bf16* hi_out, bf16* lo_out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)n * HID) return;
+  const float h = __bfloat162float(H1[i]) + __bfloat162float(H1lo[i]);
+  const float v = h > 0.f ? dz[i] : 0.f;
+  dz[i] = v;
+  const bf16 hi = __float2bfloat16(v);
+  hi_out[i] = hi;
+  lo_out[i] = __float2bfloat16(v - __bfloat162float(hi));
+}
+
+// column sums over the batch: gb2, gW3 (from dy, W3, H2 in FP32) and gb1
+// (from the FP32 dZ1), gb3
+__global__ void col_sums(const float* __restrict__ dy, const bf16* __restrict__ W3, const float* __restrict__ H2,
+                         const float* __restrict__ dZ1, int n, float* grads) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < HID) {
+    float b2 = 0.f, w3 = 0.f, b1 = 0.f;
+    const float w3j = __bfloat162float(W3[j]);
+    for (int m = 0; m < n; ++m) {
+      const float h = H2[(long)m * HID + j];
+      b2 += h > 0.f ? dy[m] * w3j : 0.f;
+      w3 += dy[m] * h;
+      b1 += dZ1[(long)m * HID + j];
+    }
+    grads[OB2 + j] = b2;
+    grads[OW3 + j] = w3;
+    grads[OB1 + j] = b1;
+  } else if (j == HID) {
+    float s = 0.f;
+    for (int m = 0; m < n; ++m) s += dy[m];
+    grads[OB3] = s;
+  }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+__global__ void to_bf16(const float* __restrict__ src, bf16* __restrict__ dst, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16(src[i]);
+}
+
+// batch gather: rows perm[b0 + i] of the full (device) training set
+__global__ void gather_rows(const float* __restrict__ X, const float* __restrict__ t, const int* __restrict__ perm,
+                            int b0, int nb, bf16* Xb, float* tb) {
+  const int i = blockIdx.x;
+  if (i >= nb) return;
+  const int r = perm[b0 + i];
+  for (int j = threadIdx.x; j < IN; j += blockDim.x) Xb[(long)i * IN + j] = __float2bfloat16(X[(long)r * IN + j]);
+  if (threadIdx.x == 0) tb[i] = t[r];
+}
+
+// genotype encoding: 20 brick slots x (present, parent/20, face/5, rot/3,
+// CPG weight), coupling weights of bricks 2..20, zeros
+__global__ void encode_kernel(const int8_t* __restrict__ parent, const int8_t* __restrict__ face,
+                              const int8_t* __restrict__ rot, const float* __restrict__ w_int,
+                              const float* __restrict__ w_cpl, const int* __restrict__ nbod, int n, float* X) {
+  const int r = blockIdx.x;
+  const int j = threadIdx.x;
+  if (r >= n || j >= IN) return;
+  const int nb = nbod[r];
+  float x = 0.f;
+  if (j < 100) {
+    const int i = j / 5, f = j % 5, b = i + 1;
+    if (b < nb) {
+      const long o = (long)r * 32 + b;
+      if (f == 0) x = 1.f;
+      else if (f == 1) x = (float)parent[o] / 20.f;
+      else if (f == 2) x = (float)face[o] / 5.f;
+      else if (f == 3) x = (float)rot[o] / 3.f;
+      else x = w_int[o];
+    }
+  } else if (j < 119) {
+    const int b = j - 100 + 2;
+    if (b < nb) x = w_cpl[(long)r * 32 + b];
+  }
+  X[(long)r * IN + j] = x;
+}
+
+// monotone float -> uint32 key (larger float, larger key)
+__device__ __forceinline__ unsigned fkey(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Top-k in one block: radix select of the k-th largest key (4 passes of 8
+// bits), then an index-ordered compaction (ties to the lower index) and a
+// bitonic sort of the selection by (key descending, index ascending).
+__global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ s, int n, int k, int* out,
+                                                    unsigned long long* work) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned sh_prefix, sh_mask, sh_kk;
+  __shared__ int scan[1024];
+  const int tid = threadIdx.x;
+  if (tid == 0) { sh_prefix = 0u; sh_mask = 0u; sh_kk = (unsigned)k; }
+  __syncthreads();
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    if (tid < 256) hist[tid] = 0u;
+    __syncthreads();
+    const unsigned prefix = sh_prefix, mask = sh_mask;
+    for (int i = tid; i < n; i += blockDim.x) {
+      const unsigned key = fkey(s[i]);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned kk = sh_kk, cum = 0;
+      int d = 255;
+      for (; d > 0; --d) {
+        if (cum + hist[d] >= kk) break;
+        cum += hist[d];
+      }
+      sh_kk = kk - cum;
+      sh_prefix = prefix | ((unsigned)d << shift);
+      sh_mask = mask | (255u << shift);
+    }
+    __syncthreads();
+  }
+  const unsigned T = sh_prefix;
+  const int ties_needed = (int)sh_kk;
+  // contiguous chunk per thread keeps index order
+  const int chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = tid * chunk, hi = min(n, lo + chunk);
+  int ties = 0;
+  for (int i = lo; i < hi; ++i) ties += fkey(s[i]) == T ? 1 : 0;
+  scan[tid] = ties;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int v = tid >= o ? scan[tid - o] : 0;
+    __syncthreads();
+    scan[tid] += v;
+    __syncthreads();
+  }
+  int tie_before = scan[tid] - ties;
+  __syncthreads();
+  int sel = 0;
+  {
+    int tb = tie_before;
+    for (int i = lo; i < hi; ++i) {
+      const unsigned key = fkey(s[i]);
+      if (key > T) ++sel;
+      else if (key == T) { if (tb < ties_needed) ++sel; ++tb; }
+    }
+  }
+  scan[tid] = sel;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int v = tid >= o ? scan[tid - o] : 0;
+    __syncthreads();
+    scan[tid] += v;
+    __syncthreads();
+  }
+  int pos = scan[tid] - sel;
+  {
+    int tb = tie_before;
+    for (int i = lo; i < hi; ++i) {
+      const unsigned key = fkey(s[i]);
+      bool take = false;
+      if (key > T) take = true;
+      else if (key == T) { take = tb < ties_needed; ++tb; }
+      if (take) work[pos++] = ((unsigned long long)(~key) << 32) | (unsigned)i;
+    }
+  }
+  __syncthreads();
+  // bitonic sort ascending of (~key, index) = key descending, index ascending
+  int P2 = 1;
+  while (P2 < k) P2 <<= 1;
+  for (int i = k + tid; i < P2; i += blockDim.x) work[i] = ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= P2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < P2; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const unsigned long long a = work[i], b = work[j];
+          if ((a > b) == up) { work[i] = b; work[j] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < k; i += blockDim.x) out[i] = (int)(work[i] & 0xffffffffu);
+}
+
+uint64_t splitmix(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double uniform01(uint64_t& x) { return (double)(splitmix(x) >> 11) * (1.0 / 9007199254740992.0); }
+
+}  // namespace
+
+struct sur_ctx {
+  sur_config cfg{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float* p = nullptr;      // FP32 master parameters
+  float* g = nullptr;      // gradients
+  float* m = nullptr;      // Adam moments
+  float* v = nullptr;
+  bf16* w1b = nullptr;     // BF16 weight copies
+  bf16* w2b = nullptr;
+  bf16* w3b = nullptr;
+  bf16* xb = nullptr;      // batch activations
+  bf16* h1 = nullptr;
+  bf16* h2 = nullptr;
+  bf16* dz2 = nullptr;
+  bf16* dz1 = nullptr;
+  bf16* dz2lo = nullptr;
+  bf16* dz1lo = nullptr;
+  bf16* h1lo = nullptr;
+  bf16* h2lo = nullptr;
+  float* h2f = nullptr;
+  float* z2f = nullptr;
+  float* dz1f = nullptr;
+  float* y = nullptr;
+  float* dy = nullptr;
+  float* tb = nullptr;
+  float* part = nullptr;
+  float* xfull = nullptr;  // training set / inputs on the device
+  float* tfull = nullptr;
+  int* perm = nullptr;
+  size_t cap_rows = 0;
+  long step = 0;
+  double mu = 0.0, sigma = 1.0;
+  unsigned long long* topk_work = nullptr;
+  float* scores = nullptr;
+  int* idx = nullptr;
+  size_t cap_scores = 0;
+};
+
+namespace {
+
+const char* g_err = "";
+
+int fail(sur_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(ctx, SUR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+cudaError_t launch_gemm(cudaStream_t st, const GemmArgs& g) {
+  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
+  gemm_bf16<<<grid, 128, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t refresh_bf16(sur_ctx* c) {
+  to_bf16<<<(HID * IN + 255) / 256, 256, 0, c->stream>>>(c->p + OW1, c->w1b, HID * IN);
+  to_bf16<<<(HID * HID + 255) / 256, 256, 0, c->stream>>>(c->p + OW2, c->w2b, HID * HID);
+  to_bf16<<<1, 256, 0, c->stream>>>(c->p + OW3, c->w3b, HID);
+  return cudaGetLastError();
+}
+
+// forward of a batch already in c->xb; y in c->y.  Hidden activations are
+// carried as BF16 pairs (hi + lo) and each GEMM consuming them runs on both
+// parts, so the forward pass rounds only the weights and inputs to BF16.
+cudaError_t forward_batch(sur_ctx* c, int n) {
+  GemmArgs g{};
+  g.M = n; g.N = HID; g.K = IN;
+  g.A = c->xb; g.lam = IN; g.lak = 1;
+  g.B = c->w1b; g.lbn = IN; g.lbk = 1;
+  g.Cb = c->h1; g.Cb_lo = c->h1lo; g.ldc = HID; g.bias = c->p + OB1; g.epi = EPI_BIAS_RELU_BF16;
+  cudaError_t e = launch_gemm(c->stream, g);
+  if (e != cudaSuccess) return e;
+  for (int part = 0; part < 2; ++part) {
+    GemmArgs h{};
+    h.M = n; h.N = HID; h.K = HID;
+    h.A = part ? c->h1lo : c->h1; h.lam = HID; h.lak = 1;
+    h.B = c->w2b; h.lbn = HID; h.lbk = 1;
+    h.Cf = c->z2f; h.ldc = HID; h.epi = part ? EPI_F32_ADD : EPI_F32;
+    e = launch_gemm(c->stream, h);
+    if (e != cudaSuccess) return e;
+  }
+  bias_relu_split<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->z2f, c->p + OB2, n, c->h2f, c->h2,
+                                                                           c->h2lo);
+  out_layer<<<(n + 7) / 8, 256, 0, c->stream>>>(c->h2f, c->w3b, c->p + OB3, n, c->y);
+  return cudaGetLastError();
+}
+
+// gradients of the batch (targets in c->tb) into c->g; loss partials in c->part.
+// The backward operands dZ2 and dZ1 are carried as BF16 pairs (hi + lo) and
+// every GEMM that consumes them runs on both parts, so their rounding is
+// ~2^-16 instead of BF16's 2^-8.
+cudaError_t backward_batch(sur_ctx* c, int n) {
+  const int nblk = (n + 255) / 256;
+  loss_grad<<<nblk, 256, 0, c->stream>>>(c->y, c->tb, n, c->dy, c->part);
+  dz2_kernel<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->dy, c->w3b, c->h2f, n, c->dz2, c->dz2lo);
+  cudaError_t e;
+  // dW2(i, j) = sum_m dZ2(m, i) H1(m, j): hi*hi + lo*hi + hi*lo
+  for (int part = 0; part < 3; ++part) {
+    GemmArgs g{};
+    g.M = HID; g.N = HID; g.K = n;
+    g.A = part == 1 ? c->dz2lo : c->dz2; g.lam = 1; g.lak = HID;
+    g.B = part == 2 ? c->h1lo : c->h1; g.lbn = 1; g.lbk = HID;
+    g.Cf = c->g + OW2; g.ldc = HID; g.epi = part ? EPI_F32_ADD : EPI_F32;
+    e = launch_gemm(c->stream, g);
+    if (e != cudaSuccess) return e;
+  }
+  // dH1(m, j) = sum_i dZ2(m, i) W2(i, j), in FP32 (hi part, then lo part added)
+  for (int part = 0; part < 2; ++part) {
+    GemmArgs h{};
+    h.M = n; h.N = HID; h.K = HID;
+    h.A = part ? c->dz2lo : c->dz2; h.lam = HID; h.lak = 1;
+    h.B = c->w2b; h.lbn = 1; h.lbk = HID;
+    h.Cf = c->dz1f; h.ldc = HID; h.epi = part ? EPI_F32_ADD : EPI_F32;
+    e = launch_gemm(c->stream, h);
+    if (e != cudaSuccess) return e;
+  }
+  relu_mask_split<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->dz1f, c->h1, c->h1lo, n, c->dz1,
+                                                                           c->dz1lo);
+  // dW1(i, j) = sum_m dZ1(m, i) X(m, j)
+  for (int part = 0; part < 2; ++part) {
+    GemmArgs w{};
+    w.M = HID; w.N = IN; w.K = n;
+    w.A = part ? c->dz1lo : c->dz1; w.lam = 1; w.lak = HID;
+    w.B = c->xb; w.lbn = 1; w.lbk = IN;
+    w.Cf = c->g + OW1; w.ldc = IN; w.epi = part ? EPI_F32_ADD : EPI_F32;
+    e = launch_gemm(c->stream, w);
+    if (e != cudaSuccess) return e;
+  }
+  col_sums<<<(HID + 1 + 127) / 128, 128, 0, c->stream>>>(c->dy, c->w3b, c->h2f, c->dz1f, n, c->g);
+  return cudaGetLastError();
+}
+
+cudaError_t adam_update(sur_ctx* c) {
+  c->step += 1;
+  const double bc1 = 1.0 - std::pow((double)c->cfg.beta1, (double)c->step);
+  const double bc2 = 1.0 - std::pow((double)c->cfg.beta2, (double)c->step);
+  adam_kernel<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->p, c->g, c->m, c->v, NP, c->cfg.lr, c->cfg.beta1,
+                                                     c->cfg.beta2, c->cfg.eps, (float)bc1, (float)bc2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return refresh_bf16(c);
+}
+
+int ensure_rows(sur_ctx* ctx, size_t n) {
+  if (n <= ctx->cap_rows) return SUR_OK;
+  cudaFree(ctx->xfull);
+  cudaFree(ctx->tfull);
+  cudaFree(ctx->perm);
+  ctx->xfull = nullptr; ctx->tfull = nullptr; ctx->perm = nullptr; ctx->cap_rows = 0;
+  if (dalloc(&ctx->xfull, n * IN) != cudaSuccess || dalloc(&ctx->tfull, n) != cudaSuccess ||
+      dalloc(&ctx->perm, n) != cudaSuccess)
+    return fail(ctx, SUR_ENOMEM, "device allocation for the training set failed");
+  ctx->cap_rows = n;
+  return SUR_OK;
+}
+
+int ensure_scores(sur_ctx* ctx, size_t n) {
+  if (n <= ctx->cap_scores) return SUR_OK;
+  cudaFree(ctx->scores);
+  cudaFree(ctx->idx);
+  ctx->scores = nullptr; ctx->idx = nullptr; ctx->cap_scores = 0;
+  if (dalloc(&ctx->scores, n) != cudaSuccess || dalloc(&ctx->idx, n) != cudaSuccess)
+    return fail(ctx, SUR_ENOMEM, "device allocation for scores failed");
+  ctx->cap_scores = n;
+  return SUR_OK;
+}
+
+void free_all(sur_ctx* c) {
+  void* ptrs[] = {c->p, c->g, c->m, c->v, c->w1b, c->w2b, c->w3b, c->xb, c->h1, c->h2, c->dz2, c->dz1,
+                  c->dz2lo, c->dz1lo, c->h1lo, c->h2lo, c->h2f, c->z2f, c->dz1f, c->y, c->dy, c->tb, c->part, c->xfull, c->tfull, c->perm, c->topk_work, c->scores,
+                  c->idx};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+int read_loss(sur_ctx* ctx, int n, float* loss_out) {
+  const int nblk = (n + 255) / 256;
+  std::vector<float> part(nblk);
+  CK(cudaMemcpyAsync(part.data(), ctx->part, nblk * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double s = 0.0;
+  for (float x : part) s += x;
+  if (loss_out) *loss_out = (float)(s / n);
+  return SUR_OK;
+}
+
+// upload n rows of X (and t) into xfull / tfull, gather them as one batch
+int stage_batch(sur_ctx* ctx, const float* X, const float* t, int n) {
+  int rc = ensure_rows(ctx, (size_t)n);
+  if (rc != SUR_OK) return rc;
+  CK(cudaMemcpyAsync(ctx->xfull, X, (size_t)n * IN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> id(n);
+  for (int i = 0; i < n; ++i) id[i] = i;
+  CK(cudaMemcpyAsync(ctx->perm, id.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  if (t) CK(cudaMemcpyAsync(ctx->tfull, t, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  else CK(cudaMemsetAsync(ctx->tfull, 0, (size_t)n * sizeof(float), ctx->stream));
+  gather_rows<<<n, 128, 0, ctx->stream>>>(ctx->xfull, ctx->tfull, ctx->perm, 0, n, ctx->xb, ctx->tb);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SUR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sur_create(const sur_config* cfg, sur_ctx_t** out) {
+  if (!out) return SUR_EINVAL;
+  *out = nullptr;
+  if (!cfg || !(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+      !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f)) {
+    g_err = "sur_create: NULL or out-of-range configuration";
+    return SUR_EINVAL;
+  }
+  sur_ctx* ctx = new (std::nothrow) sur_ctx();
+  if (!ctx) return SUR_ENOMEM;
+  ctx->cfg = *cfg;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    g_err = "sur_create: cudaSetDevice failed";
+    delete ctx;
+    return SUR_ECUDA;
+  }
+  if (cfg->stream) {
+    ctx->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      g_err = "sur_create: cudaStreamCreate failed";
+      delete ctx;
+      return SUR_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  const size_t B = SUR_MAX_BATCH;
+  bool ok = dalloc(&ctx->p, NP) == cudaSuccess && dalloc(&ctx->g, NP) == cudaSuccess &&
+            dalloc(&ctx->m, NP) == cudaSuccess && dalloc(&ctx->v, NP) == cudaSuccess &&
+            dalloc(&ctx->w1b, (size_t)HID * IN) == cudaSuccess && dalloc(&ctx->w2b, (size_t)HID * HID) == cudaSuccess &&
+            dalloc(&ctx->w3b, (size_t)HID) == cudaSuccess && dalloc(&ctx->xb, B * IN) == cudaSuccess &&
+            dalloc(&ctx->h1, B * HID) == cudaSuccess && dalloc(&ctx->h2, B * HID) == cudaSuccess &&
+            dalloc(&ctx->dz2, B * HID) == cudaSuccess && dalloc(&ctx->dz1, B * HID) == cudaSuccess &&
+            dalloc(&ctx->dz2lo, B * HID) == cudaSuccess && dalloc(&ctx->dz1lo, B * HID) == cudaSuccess &&
+            dalloc(&ctx->h1lo, B * HID) == cudaSuccess && dalloc(&ctx->h2lo, B * HID) == cudaSuccess &&
+            dalloc(&ctx->h2f, B * HID) == cudaSuccess && dalloc(&ctx->z2f, B * HID) == cudaSuccess &&
+            dalloc(&ctx->dz1f, B * HID) == cudaSuccess && dalloc(&ctx->y, B) == cudaSuccess &&
+            dalloc(&ctx->dy, B) == cudaSuccess && dalloc(&ctx->tb, B) == cudaSuccess &&
+            dalloc(&ctx->part, (B + 255) / 256) == cudaSuccess &&
+            dalloc(&ctx->topk_work, (size_t)2 * SUR_MAX_TOPK) == cudaSuccess;
+  if (!ok) {
+    free_all(ctx);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    g_err = "sur_create: device allocation failed";
+    return SUR_ENOMEM;
+  }
+  // He-uniform weights from the seed, zero biases
+  std::vector<float> p(NP, 0.f);
+  uint64_t st = cfg->seed ^ 0x5DEECE66DULL;
+  auto fill = [&](int off, int rows, int cols) {
+    const double lim = std::sqrt(6.0 / cols);
+    for (int i = 0; i < rows * cols; ++i) p[off + i] = (float)((2.0 * uniform01(st) - 1.0) * lim);
+  };
+  fill(OW1, HID, IN);
+  fill(OW2, HID, HID);
+  fill(OW3, 1, HID);
+  *out = ctx;
+  return sur_set_params(ctx, p.data());
+}
+
+int sur_destroy(sur_ctx_t* ctx) {
+  if (!ctx) return SUR_OK;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return SUR_OK;
+}
+
+int sur_set_params(sur_ctx_t* ctx, const float* params) {
+  if (!ctx || !params) return fail(ctx, SUR_EINVAL, "sur_set_params: NULL");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaMemcpyAsync(ctx->p, params, NP * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->m, 0, NP * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->v, 0, NP * sizeof(float), ctx->stream));
+  ctx->step = 0;
+  ctx->mu = 0.0;
+  ctx->sigma = 1.0;
+  CK(refresh_bf16(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SUR_OK;
+}
+
+int sur_get_params(sur_ctx_t* ctx, float* params) {
+  if (!ctx || !params) return fail(ctx, SUR_EINVAL, "sur_get_params: NULL");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaMemcpyAsync(params, ctx->p, NP * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SUR_OK;
+}
+
+int sur_encode(sur_ctx_t* ctx, const int8_t* parent, const int8_t* face, const int8_t* rot, const float* w_int,
+               const float* w_cpl, const int32_t* n_bodies, int32_t n, float* X_out) {
+  if (!ctx) return SUR_EINVAL;
+  if (n < 1 || !parent || !face || !rot || !w_int || !w_cpl || !n_bodies || !X_out)
+    return fail(ctx, SUR_EINVAL, "sur_encode: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int8_t *dp = nullptr, *df = nullptr, *dr = nullptr;
+  float *dwi = nullptr, *dwc = nullptr, *dX = nullptr;
+  int* dn = nullptr;
+  const size_t N = (size_t)n;
+  bool ok = dalloc(&dp, N * 32) == cudaSuccess && dalloc(&df, N * 32) == cudaSuccess &&
+            dalloc(&dr, N * 32) == cudaSuccess && dalloc(&dwi, N * 32) == cudaSuccess &&
+            dalloc(&dwc, N * 32) == cudaSuccess && dalloc(&dn, N) == cudaSuccess && dalloc(&dX, N * IN) == cudaSuccess;
+  int rc = SUR_OK;
+  if (!ok) {
+    rc = fail(ctx, SUR_ENOMEM, "sur_encode: device allocation failed");
+  } else {
+    cudaMemcpyAsync(dp, parent, N * 32, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(df, face, N * 32, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dr, rot, N * 32, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dwi, w_int, N * 32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dwc, w_cpl, N * 32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dn, n_bodies, N * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    encode_kernel<<<n, IN, 0, ctx->stream>>>(dp, df, dr, dwi, dwc, dn, n, dX);
+    cudaMemcpyAsync(X_out, dX, N * IN * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) rc = fail(ctx, SUR_ECUDA, std::string("sur_encode: ") + cudaGetErrorString(e));
+  }
+  cudaFree(dp); cudaFree(df); cudaFree(dr); cudaFree(dwi); cudaFree(dwc); cudaFree(dn); cudaFree(dX);
+  return rc;
+}
+
+int sur_predict(sur_ctx_t* ctx, const float* X, int32_t n, float* y_out) {
+  if (!ctx) return SUR_EINVAL;
+  if (!X || !y_out || n < 1) return fail(ctx, SUR_EINVAL, "sur_predict: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = ensure_rows(ctx, (size_t)n);
+  if (rc != SUR_OK) return rc;
+  CK(cudaMemcpyAsync(ctx->xfull, X, (size_t)n * IN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> id(n);
+  for (int i = 0; i < n; ++i) id[i] = i;
+  CK(cudaMemcpyAsync(ctx->perm, id.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->tfull, 0, (size_t)n * sizeof(float), ctx->stream));
+  std::vector<float> tmp(SUR_MAX_BATCH);
+  for (int b0 = 0; b0 < n; b0 += SUR_MAX_BATCH) {
+    const int nb = std::min(SUR_MAX_BATCH, n - b0);
+    gather_rows<<<nb, 128, 0, ctx->stream>>>(ctx->xfull, ctx->tfull, ctx->perm, b0, nb, ctx->xb, ctx->tb);
+    CK(cudaGetLastError());
+    CK(forward_batch(ctx, nb));
+    CK(cudaMemcpyAsync(tmp.data(), ctx->y, nb * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < nb; ++i) y_out[b0 + i] = (float)(ctx->mu + ctx->sigma * (double)tmp[i]);
+  }
+  return SUR_OK;
+}
+
+int sur_gradients(sur_ctx_t* ctx, const float* X, const float* y, int32_t n, float* grads, float* loss_out) {
+  if (!ctx) return SUR_EINVAL;
+  if (!X || !y || !grads || n < 1 || n > SUR_MAX_BATCH) return fail(ctx, SUR_EINVAL, "sur_gradients: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = stage_batch(ctx, X, y, n);
+  if (rc != SUR_OK) return rc;
+  CK(forward_batch(ctx, n));
+  CK(backward_batch(ctx, n));
+  CK(cudaMemcpyAsync(grads, ctx->g, NP * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  return read_loss(ctx, n, loss_out);
+}
+
+int sur_train_step(sur_ctx_t* ctx, const float* X, const float* y, int32_t n, float* loss_out) {
+  if (!ctx) return SUR_EINVAL;
+  if (!X || !y || n < 1 || n > SUR_MAX_BATCH) return fail(ctx, SUR_EINVAL, "sur_train_step: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = stage_batch(ctx, X, y, n);
+  if (rc != SUR_OK) return rc;
+  CK(forward_batch(ctx, n));
+  CK(backward_batch(ctx, n));
+  CK(adam_update(ctx));
+  return read_loss(ctx, n, loss_out);
+}
+
+int sur_train(sur_ctx_t* ctx, const float* X, const float* y, int32_t n, int32_t epochs, int32_t batch,
+              float* loss_out) {
+  if (!ctx) return SUR_EINVAL;
+  if (!X || !y || n < 2 || epochs < 1 || batch < 1 || batch > SUR_MAX_BATCH)
+    return fail(ctx, SUR_EINVAL, "sur_train: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = ensure_rows(ctx, (size_t)n);
+  if (rc != SUR_OK) return rc;
+  double mu = 0.0, var = 0.0;
+  for (int i = 0; i < n; ++i) mu += y[i];
+  mu /= n;
+  for (int i = 0; i < n; ++i) var += (y[i] - mu) * (y[i] - mu);
+  const double sigma = std::sqrt(var / n) > 1e-12 ? std::sqrt(var / n) : 1.0;
+  std::vector<float> t(n);
+  for (int i = 0; i < n; ++i) t[i] = (float)((y[i] - mu) / sigma);
+  ctx->mu = mu;
+  ctx->sigma = sigma;
+  CK(cudaMemcpyAsync(ctx->xfull, X, (size_t)n * IN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->tfull, t.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> perm(n);
+  uint64_t st = ctx->cfg.seed * 0x2545F4914F6CDD1DULL + (uint64_t)ctx->step;
+  const int nblk_max = (batch + 255) / 256;
+  std::vector<float> part(nblk_max);
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = n - 1; i > 0; --i) {
+      const int j = (int)(splitmix(st) % (uint64_t)(i + 1));
+      std::swap(perm[i], perm[j]);
+    }
+    CK(cudaMemcpyAsync(ctx->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    double ep_loss = 0.0;
+    for (int b0 = 0; b0 < n; b0 += batch) {
+      const int nb = std::min(batch, n - b0);
+      gather_rows<<<nb, 128, 0, ctx->stream>>>(ctx->xfull, ctx->tfull, ctx->perm, b0, nb, ctx->xb, ctx->tb);
+      CK(cudaGetLastError());
+      CK(forward_batch(ctx, nb));
+      CK(backward_batch(ctx, nb));
+      CK(adam_update(ctx));
+      if (ep == epochs - 1) {
+        const int nblk = (nb + 255) / 256;
+        CK(cudaMemcpyAsync(part.data(), ctx->part, nblk * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int q = 0; q < nblk; ++q) ep_loss += part[q];
+      }
+    }
+    if (ep == epochs - 1) last = ep_loss / n;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (loss_out) *loss_out = (float)last;
+  return SUR_OK;
+}
+
+int sur_topk(sur_ctx_t* ctx, const float* scores, int32_t n, int32_t k, int32_t* idx_out) {
+  if (!ctx) return SUR_EINVAL;
+  if (!scores || !idx_out || n < 1 || k < 1 || k > n || k > SUR_MAX_TOPK)
+    return fail(ctx, SUR_EINVAL, "sur_topk: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = ensure_scores(ctx, (size_t)n);
+  if (rc != SUR_OK) return rc;
+  CK(cudaMemcpyAsync(ctx->scores, scores, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  topk_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->scores, n, k, ctx->idx, ctx->topk_work);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(idx_out, ctx->idx, (size_t)k * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SUR_OK;
+}
+
+const char* sur_last_error(const sur_ctx_t* ctx) {
+  if (!ctx) return g_err;
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

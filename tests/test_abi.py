@@ -45,8 +45,10 @@ def test_libraries_build_and_export_every_declared_symbol():
 
 
 def test_binding_lists_every_declared_entry_point():
-    decl = header_functions()["b3sim.h"]
-    assert sorted(decl) == sorted(S.EXPORTS)
+    from paper_2502_11129_b300 import surrogate as SG
+    decl = header_functions()
+    assert sorted(decl["b3sim.h"]) == sorted(S.EXPORTS)
+    assert sorted(decl["b3sur.h"]) == sorted(SG.EXPORTS)
 
 
 def test_sim_create_argument_errors_without_device():

@@ -1,0 +1,130 @@
+"""Surrogate CUDA library vs the FP64 oracle (oracle/mlp.py), through the C ABI.
+
+Tolerances (BF16 weights and activations, FP32 accumulation):
+  * forward: |y_gpu - y_ref| <= 1e-2 * max(|y_ref|, scale) per output, with
+    scale the RMS of the reference outputs;
+  * gradients: per parameter tensor |g_gpu - g_ref| / |g_ref| <= 2e-2;
+  * encoding and top-k: exact.
+"""
+import numpy as np
+import pytest
+
+from paper_2502_11129_b300 import population as P
+from paper_2502_11129_b300 import surrogate as SG
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle():
+    from oracle import mlp as M
+    return M
+
+
+def ref_params(seed):
+    M = oracle()
+    rng = np.random.default_rng(seed)
+    p = M.init_params(rng)
+    p["b1"] = rng.normal(0, 0.1, 256)
+    p["b2"] = rng.normal(0, 0.1, 256)
+    p["b3"] = rng.normal(0, 0.1, 1)
+    # float32 master weights, as the library stores them
+    return {k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}
+
+
+def test_encoding_matches_oracle_exactly():
+    M = oracle()
+    pop = P.grammar(300, seed=8)
+    s = SG.Surrogate()
+    X = s.encode(pop)
+    Xr = M.encode_population(pop)
+    assert np.abs(X - Xr).max() < 1e-7
+    s.close()
+
+
+def test_forward_matches_oracle():
+    M = oracle()
+    rng = np.random.default_rng(1)
+    p = ref_params(2)
+    X = rng.normal(size=(3000, 128)) * 0.5
+    s = SG.Surrogate()
+    s.set_params(SG.pack_params(p))
+    y = s.predict(X.astype(np.float32))
+    yr, _ = M.forward(p, X.astype(np.float32))
+    scale = np.sqrt(np.mean(yr ** 2))
+    err = np.abs(y - yr) / np.maximum(np.abs(yr), scale)
+    assert err.max() <= 1e-2, err.max()
+    s.close()
+
+
+def test_gradients_match_oracle():
+    M = oracle()
+    rng = np.random.default_rng(3)
+    p = ref_params(4)
+    X = (rng.normal(size=(1024, 128)) * 0.5).astype(np.float32)
+    t = rng.normal(size=1024).astype(np.float32)
+    s = SG.Surrogate()
+    s.set_params(SG.pack_params(p))
+    g, loss = s.gradients(X, t)
+    gr, lr_ = M.backward(p, X, t)
+    gd = SG.unpack_params(g)
+    assert abs(loss - lr_) <= 1e-2 * lr_
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        rel = np.linalg.norm(gd[k] - gr[k]) / np.linalg.norm(gr[k])
+        assert rel <= 2e-2, (k, rel)
+    s.close()
+
+
+def test_one_adam_step_matches_oracle():
+    M = oracle()
+    rng = np.random.default_rng(5)
+    p = ref_params(6)
+    X = (rng.normal(size=(512, 128)) * 0.5).astype(np.float32)
+    t = rng.normal(size=512).astype(np.float32)
+    s = SG.Surrogate(lr=1e-3)
+    s.set_params(SG.pack_params(p))
+    s.train_step(X, t)
+    new = SG.unpack_params(s.get_params())
+    g, _ = M.backward(p, X, t)
+    zeros = {k: np.zeros_like(v) for k, v in p.items()}
+    p2, _, _ = M.adam_step(p, g, zeros, zeros, 1, lr=1e-3)
+    # first step moves each weight by lr * sign(g) (where |g| >> eps): compare steps
+    for k in p:
+        step_gpu = new[k] - p[k]
+        step_ref = p2[k] - p[k]
+        agree = np.mean(np.abs(step_gpu - step_ref) <= 1e-5)
+        assert agree >= 0.98, (k, agree)
+    s.close()
+
+
+def test_training_reduces_loss_and_learns_a_function():
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(8192, 128)).astype(np.float32) * 0.5
+    w = rng.normal(size=128)
+    y = (np.tanh(X @ w / 8) + 0.1 * (X[:, 0] ** 2)).astype(np.float32)
+    s = SG.Surrogate(seed=3, lr=1e-3)
+    l0 = s.train(X, y, epochs=1, batch=512)
+    l1 = s.train(X, y, epochs=20, batch=512)
+    assert l1 < 0.2 * l0, (l0, l1)
+    pred = s.predict(X[:2000])
+    assert np.corrcoef(pred, y[:2000])[0, 1] > 0.95
+    s.close()
+
+
+def test_topk_matches_oracle_with_ties():
+    M = oracle()
+    rng = np.random.default_rng(9)
+    s = SG.Surrogate()
+    for n, k in ((65536, 4096), (1000, 37), (5000, 5000)):
+        sc = rng.integers(-300, 300, size=n).astype(np.float32) / 7.0
+        idx = s.topk(sc, k)
+        assert np.array_equal(idx, M.topk(sc, k)), (n, k)
+    s.close()
+
+
+def test_argument_errors():
+    s = SG.Surrogate()
+    with pytest.raises(SG.SurrogateError, match="SUR_EINVAL"):
+        s.topk(np.zeros(10, np.float32), 20)
+    with pytest.raises(SG.SurrogateError, match="SUR_EINVAL"):
+        s.gradients(np.zeros((SG.MAX_BATCH + 1, 128), np.float32), np.zeros(SG.MAX_BATCH + 1, np.float32))
+    s.close()
