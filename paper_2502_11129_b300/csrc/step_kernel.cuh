@@ -86,6 +86,7 @@ struct WarpSmem {
   int parent[32];
   unsigned path[32];
   unsigned keep[kCand / 32];
+  float Yrow[32][33];      // contact rows under construction (lane = row)
 };
 
 __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFull, x, src); }
@@ -219,16 +220,23 @@ __device__ __noinline__ int box_box_lane(const WarpSmem& sm, const float* __rest
   float fbest = 0.f, ebest = 0.f, min_ov = 0.f;
   int fi = -1, ei = -1;
   float Le[3] = {0.f, 0.f, 0.f};
+  auto pick = [](const float (*X)[3], int k, float* o) {
 #pragma unroll
+    for (int t = 0; t < 3; ++t) o[t] = k == 0 ? X[0][t] : (k == 1 ? X[1][t] : X[2][t]);
+  };
+#pragma unroll 1
   for (int e = 0; e < 15; ++e) {
     float L[3];
     bool valid = true;
     if (e < 3) {
-      L[0] = Ax[e][0]; L[1] = Ax[e][1]; L[2] = Ax[e][2];
+      pick(Ax, e, L);
     } else if (e < 6) {
-      L[0] = Bx[e - 3][0]; L[1] = Bx[e - 3][1]; L[2] = Bx[e - 3][2];
+      pick(Bx, e - 3, L);
     } else {
-      cross3(Ax[(e - 6) / 3], Bx[(e - 6) % 3], L);
+      float ai[3], bj[3];
+      pick(Ax, (e - 6) / 3, ai);
+      pick(Bx, (e - 6) % 3, bj);
+      cross3(ai, bj, L);
       const float nl = sqrtf(dot3(L, L));
       if (nl < 1e-6f) valid = false;
       else { L[0] /= nl; L[1] /= nl; L[2] /= nl; }
@@ -723,17 +731,16 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     int ncand = 0;
     if (P.ground) {
       unsigned mask8 = 0;
-      float zdepth[8];
       const float h0 = fld(F_HALF), h1 = fld(F_HALF + 1), h2 = fld(F_HALF + 2);
       const float c0 = fld(F_COM), c1 = fld(F_COM + 1), c2 = fld(F_COM + 2);
+      auto vheight = [&](int k) {
+        const double l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
+        return (double)p0z + (hzb + (hz0 * l0 + hz1 * l1 + hz2 * l2));
+      };
       if (body) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const double l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
-          const double z = (double)p0z + (hzb + (hz0 * l0 + hz1 * l1 + hz2 * l2));
-          if (z < 0.0) mask8 |= 1u << k;
-          zdepth[k] = (float)(-z);
-        }
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k)
+          if (vheight(k) < 0.0) mask8 |= 1u << k;
       }
       const int cnt = __popc(mask8);
       int incl = cnt;
@@ -744,16 +751,14 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       int off = incl - cnt;
       const float up[3] = {0.f, 0.f, 1.f};
+      for (unsigned mm = mask8; mm; mm &= mm - 1) {
+        const int k = __ffs(mm) - 1;
+        const float l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
+        float pr[3];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (mask8 & (1u << k)) {
-          const float l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
-          float pr[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) pr[a] = r[a] + (R[3 * a] * l0 + R[3 * a + 1] * l1 + R[3 * a + 2] * l2);
-          if (off < kCand) put_candidate(cand, off, pr, up, zdepth[k], lane, 255);
-          ++off;
-        }
+        for (int a = 0; a < 3; ++a) pr[a] = r[a] + (R[3 * a] * l0 + R[3 * a + 1] * l1 + R[3 * a + 2] * l2);
+        if (off < kCand) put_candidate(cand, off, pr, up, (float)(-vheight(k)), lane, 255);
+        ++off;
       }
       ncand = shfi(incl, 31);
       if (ncand > kCand) st |= 8u;
@@ -876,45 +881,45 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       float wa[3];
       cross3(pr, d, wa);
-      float y[32];
+      // J_r into this lane's row buffer; compact loops keep the code small
+      float* yr = sm.Yrow[lane];
       float jv = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float Jj = 0.f;
-        if (j < nv) {
-          float coef;
-          if (j < 6) coef = sroot;
-          else {
-            const int bj = j - 5;
-            coef = (float)((int)((pa >> bj) & 1u) - (int)((pb >> bj) & 1u));
-          }
-          Jj = coef * (sm.S[0][j] * wa[0] + sm.S[1][j] * wa[1] + sm.S[2][j] * wa[2] + sm.S[3][j] * d[0] +
-                       sm.S[4][j] * d[1] + sm.S[5][j] * d[2]);
-          jv += Jj * sm.vfree[j];
+#pragma unroll 1
+      for (int j = 0; j < nv; ++j) {
+        float coef;
+        if (j < 6) coef = sroot;
+        else {
+          const int bj = j - 5;
+          coef = (float)((int)((pa >> bj) & 1u) - (int)((pb >> bj) & 1u));
         }
-        y[j] = Jj;
+        const float Jj = coef * (sm.S[0][j] * wa[0] + sm.S[1][j] * wa[1] + sm.S[2][j] * wa[2] + sm.S[3][j] * d[0] +
+                                 sm.S[4][j] * d[1] + sm.S[5][j] * d[2]);
+        jv += Jj * sm.vfree[j];
+        yr[j] = Jj;
       }
       // forward substitution y <- L^-1 y, L broadcast from shared memory
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        if (i < nv) {
-          const int ti = tri(i);
-          float t = y[i];
-#pragma unroll
-          for (int kk = 0; kk < i; ++kk) t -= sm.M[ti + kk] * y[kk];
-          y[i] = t * sm.invd[i];
-        }
-      }
       float aa = 0.f;
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i < nv) aa += y[i] * y[i];
+#pragma unroll 1
+      for (int i = 0; i < nv; ++i) {
+        const float* Li = sm.M + tri(i);
+        float t0 = yr[i], t1 = 0.f;
+        int kk = 0;
+#pragma unroll 1
+        for (; kk + 1 < i; kk += 2) {
+          t0 -= Li[kk] * yr[kk];
+          t1 -= Li[kk + 1] * yr[kk + 1];
+        }
+        if (kk < i) t0 -= Li[kk] * yr[kk];
+        const float yi = (t0 + t1) * sm.invd[i];
+        yr[i] = yi;
+        aa += yi * yi;
+      }
       if (act) {
         float4* dst = reinterpret_cast<float4*>(Yg + (size_t)row * 32);
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < 8; ++i)
-          dst[i] = make_float4(i * 4 + 0 < nv ? y[i * 4 + 0] : 0.f, i * 4 + 1 < nv ? y[i * 4 + 1] : 0.f,
-                               i * 4 + 2 < nv ? y[i * 4 + 2] : 0.f, i * 4 + 3 < nv ? y[i * 4 + 3] : 0.f);
+          dst[i] = make_float4(i * 4 + 0 < nv ? yr[i * 4 + 0] : 0.f, i * 4 + 1 < nv ? yr[i * 4 + 1] : 0.f,
+                               i * 4 + 2 < nv ? yr[i * 4 + 2] : 0.f, i * 4 + 3 < nv ? yr[i * 4 + 3] : 0.f);
         const float Rr = P.kappa * aa;
         // a row that no dof can move (J = 0) carries no impulse: 1/(A+R) = 0
         const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
