@@ -74,19 +74,23 @@ constexpr size_t kScratchFloats = kDbgOffset + 32 + 4 * kCapMax + 16;
 
 __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
 
-struct WarpSmem {
+struct __align__(16) WarpSmem {
   float R[9][32];          // body rotations (lane = body)
   float r[3][32];          // body frame origins relative to the core origin
   float c[3][32];          // box centres relative to the core origin
   float S[6][32];          // dof-indexed motion subspace columns
-  float acc[16][32];       // per-body f (6) + composite inertia (10)
+  union {
+    float acc[16][33];     // per-body f (6) + composite inertia (10), padded (steps 1-4)
+    float Yt[32][32];      // contact rows under construction, [dof][row] (step 7),
+                           // then the Delassus matrix [row][row] (step 8)
+  };
   float M[kTri];           // mass matrix, then its Cholesky factor (packed lower)
   float invd[32];
   float vfree[32];
   int parent[32];
   unsigned path[32];
   unsigned keep[kCand / 32];
-  float Yrow[32][33];      // contact rows under construction (lane = row)
+  unsigned long long ph[kPhases];  // per-phase SM cycles (inspection only)
 };
 
 __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFull, x, src); }
@@ -437,16 +441,16 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   float lam_a[3] = {0.f, 0.f, 0.f}, lam_b[3] = {0.f, 0.f, 0.f};  // impulses of contacts lane, lane + 32
 
   const long long t_start = clock64();
-  // per-phase SM cycles (kept on every lane, written by lane 0 at the end):
+  // per-phase SM cycles (accumulated by lane 0 in shared memory):
   // 0 CPG+FK, 1 inertias+RNEA+CRBA, 2 Cholesky+v_free, 3 ground contacts,
   // 4 box/box, 5 cap, 6 contact rows, 7 Gauss-Seidel, 8 integration
-  unsigned long long ph[kPhases] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (lane < kPhases) sm.ph[lane] = 0ull;
   long long tph = clock64();
-#define B3_PHASE(i)                                   \
-  do {                                                \
-    const long long t_ = clock64();                   \
-    ph[i] += (unsigned long long)(t_ - tph);          \
-    tph = t_;                                         \
+#define B3_PHASE(i)                                                  \
+  do {                                                               \
+    const long long t_ = clock64();                                  \
+    if (lane == 0) sm.ph[i] += (unsigned long long)(t_ - tph);       \
+    tph = t_;                                                        \
   } while (0)
   float* cand = scratch + (size_t)var * kScratchFloats;
   float* Yg = cand + kYOffset;
@@ -855,6 +859,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 
     B3_PHASE(5);
     // ---------------- 7. contact rows: Y_r = L^-1 J_r^T and Gauss-Seidel constants (lane = row)
+    float w_row = 0.f;  // with at most 32 rows: this lane's row residual J_r v_free - bias
     for (int r0 = 0; r0 < 3 * nc; r0 += 32) {
       const int row = r0 + lane;
       const bool act = row < 3 * nc;
@@ -881,8 +886,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       float wa[3];
       cross3(pr, d, wa);
-      // J_r into this lane's row buffer; compact loops keep the code small
-      float* yr = sm.Yrow[lane];
+      // J_r into this lane's column of Yt ([dof][row]); compact loops keep the code small
+      float* yr = &sm.Yt[0][lane];
       float jv = 0.f;
 #pragma unroll 1
       for (int j = 0; j < nv; ++j) {
@@ -895,31 +900,31 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         const float Jj = coef * (sm.S[0][j] * wa[0] + sm.S[1][j] * wa[1] + sm.S[2][j] * wa[2] + sm.S[3][j] * d[0] +
                                  sm.S[4][j] * d[1] + sm.S[5][j] * d[2]);
         jv += Jj * sm.vfree[j];
-        yr[j] = Jj;
+        yr[32 * j] = Jj;
       }
+      for (int j = nv; j < 32; ++j) yr[32 * j] = 0.f;
       // forward substitution y <- L^-1 y, L broadcast from shared memory
       float aa = 0.f;
 #pragma unroll 1
       for (int i = 0; i < nv; ++i) {
         const float* Li = sm.M + tri(i);
-        float t0 = yr[i], t1 = 0.f;
+        float t0 = yr[32 * i], t1 = 0.f;
         int kk = 0;
 #pragma unroll 1
         for (; kk + 1 < i; kk += 2) {
-          t0 -= Li[kk] * yr[kk];
-          t1 -= Li[kk + 1] * yr[kk + 1];
+          t0 -= Li[kk] * yr[32 * kk];
+          t1 -= Li[kk + 1] * yr[32 * (kk + 1)];
         }
-        if (kk < i) t0 -= Li[kk] * yr[kk];
+        if (kk < i) t0 -= Li[kk] * yr[32 * kk];
         const float yi = (t0 + t1) * sm.invd[i];
-        yr[i] = yi;
+        yr[32 * i] = yi;
         aa += yi * yi;
       }
       if (act) {
         float4* dst = reinterpret_cast<float4*>(Yg + (size_t)row * 32);
 #pragma unroll 1
         for (int i = 0; i < 8; ++i)
-          dst[i] = make_float4(i * 4 + 0 < nv ? yr[i * 4 + 0] : 0.f, i * 4 + 1 < nv ? yr[i * 4 + 1] : 0.f,
-                               i * 4 + 2 < nv ? yr[i * 4 + 2] : 0.f, i * 4 + 3 < nv ? yr[i * 4 + 3] : 0.f);
+          dst[i] = make_float4(yr[32 * (4 * i)], yr[32 * (4 * i + 1)], yr[32 * (4 * i + 2)], yr[32 * (4 * i + 3)]);
         const float Rr = P.kappa * aa;
         // a row that no dof can move (J = 0) carries no impulse: 1/(A+R) = 0
         const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
@@ -929,9 +934,10 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         cs[0] = bias;
         cs[1] = inv;
         cs[2] = Rr;
+        w_row = bias;
       }
+      __syncwarp();
     }
-    __syncwarp();
     // tangent/normal coupling A_tn = Y_t . Y_n of each contact (lane = contact)
     for (int k0 = 0; k0 < nc; k0 += 32) {
       const int k = k0 + lane;
@@ -957,10 +963,75 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     __syncwarp();
 
     B3_PHASE(6);
-    // ---------------- 8. soft projected Gauss-Seidel (lane = dof, u = L^T (v - v_free));
-    // the impulses of contact k live in lane k & 31 (slot k >> 5)
+    // ---------------- 8. soft projected Gauss-Seidel
     float u = 0.f;
-    if (nc > 0) {
+    if (nc > 0 && 3 * nc <= 32) {
+      // Up to 10 contacts: sweep in contact space.  Lane r keeps row r of the
+      // Delassus matrix A = J M^-1 J^T = Y Y^T (shared memory), its impulse
+      // lam_r and its residual w_r = J_r v_free - bias_r + sum_s A_rs lam_s;
+      // a contact update reads its three residuals with shuffles and adds
+      // A_r. dlam to every row.  Same iteration as the dof-space sweep below.
+      {
+        float a[32];
+#pragma unroll
+        for (int c2 = 0; c2 < 32; ++c2) a[c2] = 0.f;
+#pragma unroll 1
+        for (int j = 0; j < nv; ++j) {
+          const float own = sm.Yt[j][lane];
+          const float4* Yj = reinterpret_cast<const float4*>(sm.Yt[j]);
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 y4 = Yj[q4];
+            a[4 * q4] += own * y4.x;
+            a[4 * q4 + 1] += own * y4.y;
+            a[4 * q4 + 2] += own * y4.z;
+            a[4 * q4 + 3] += own * y4.w;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c2 = 0; c2 < 32; ++c2) sm.Yt[c2][lane] = a[c2];  // [col][row], symmetric
+        __syncwarp();
+      }
+      float lam = 0.f, w = w_row;
+      const float4* c4 = reinterpret_cast<const float4*>(cstg);
+      float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
+      float an = sm.Yt[0][lane], a1 = sm.Yt[1][lane], a2 = sm.Yt[2][lane];
+      for (int it = 0; it < P.iters; ++it) {
+        for (int k = 0; k < nc; ++k) {
+          const int kn = (k + 1 < nc) ? k + 1 : 0;
+          const float nan0 = sm.Yt[3 * kn][lane], na1 = sm.Yt[3 * kn + 1][lane], na2 = sm.Yt[3 * kn + 2][lane];
+          const float4 na = c4[3 * kn], nb4 = c4[3 * kn + 1], nc4 = c4[3 * kn + 2];
+          const int r = 3 * k;
+          const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
+          const float ln = shf(lam, r), l1 = shf(lam, r + 1), l2 = shf(lam, r + 2);
+          const float gn = wn + ca.z * ln;
+          const float lnn = fmaxf(0.f, ln - gn * ca.y);
+          const float dn = lnn - ln;
+          const float g1 = w1 + cc4.y * dn + cb4.y * l1;
+          const float g2 = w2 + cc4.z * dn + cc4.x * l2;
+          float l1t = l1 - g1 * cb4.x;
+          float l2t = l2 - g2 * cb4.w;
+          const float lim = P.mu * lnn;
+          const float nt2 = l1t * l1t + l2t * l2t;
+          if (nt2 > lim * lim) {
+            const float sc = lim * rsqrtf(nt2);
+            l1t *= sc;
+            l2t *= sc;
+          }
+          w += an * dn + a1 * (l1t - l1) + a2 * (l2t - l2);
+          lam = lane == r ? lnn : (lane == r + 1 ? l1t : (lane == r + 2 ? l2t : lam));
+          an = nan0; a1 = na1; a2 = na2;
+          ca = na; cb4 = nb4; cc4 = nc4;
+        }
+      }
+      // u = sum_r Y_r lam_r (lane = dof)
+      for (int r = 0; r < 3 * nc; ++r) u += shf(lam, r) * Yg[(size_t)r * 32 + lane];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) lam_a[t] = shf(lam, (3 * lane + t) & 31);
+    } else if (nc > 0) {
+      // dof space (lane = dof, u = L^T (v - v_free)); the impulses of contact
+      // k live in lane k & 31 (slot k >> 5)
       float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
       const float4* c4 = reinterpret_cast<const float4*>(cstg);
       float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
@@ -1068,12 +1139,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   float* dbg = scratch + (size_t)var * kScratchFloats + kDbgOffset;
   dbg[lane] = vfree_last;
   if (lane == 31) dbg[31] = n_steps > 0 ? (float)(clock64() - t_start) / (float)n_steps : 0.f;
-  if (lane < kPhases) {
-    unsigned long long mine = 0;
-#pragma unroll
-    for (int i = 0; i < kPhases; ++i) mine = (lane == i) ? ph[i] : mine;
-    dbg[32 + 4 * kCapMax + lane] = n_steps > 0 ? (float)mine / (float)n_steps : 0.f;
-  }
+  if (lane < kPhases) dbg[32 + 4 * kCapMax + lane] = n_steps > 0 ? (float)sm.ph[lane] / (float)n_steps : 0.f;
   if (n_steps > 0) {
     if (lane < nc_last) {
       dbg[32 + 4 * lane] = lam_a[0];
