@@ -269,7 +269,8 @@ def run_ours(args, world, rank, local, dist):
                                                                              "(256 MiB write)",
                       "contacts_per_variant_step": contacts_per_vs, "frozen_variants": frozen,
                       "parallelism": f"dp{world} (independent robots per GPU)"},
-           "gpu_launches": args.steps * launches_per_chunk, "e2e": e2e, "clocks": clk}
+           # per launch chunk: cost_histogram + cost_scatter (slowest-first order) + step_kernel
+           "gpu_launches": args.steps * launches_per_chunk * 3, "e2e": e2e, "clocks": clk}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from paper_2502_11129_b300 import population as P2

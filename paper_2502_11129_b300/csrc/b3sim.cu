@@ -46,6 +46,8 @@ struct sim_ctx {
   Counters* d_counters = nullptr;
   float* d_scratch = nullptr;
   int* d_lastnc = nullptr;
+  int* d_order = nullptr;        // launch slot -> packed index (slowest first)
+  unsigned* d_order_hist = nullptr;  // cost-bucket counts and cursors (2 x kCostBuckets)
   float* d_stage = nullptr;  // caller-order staging: q | v | s rows
   unsigned* d_stage_st = nullptr;
   StepParams P{};
@@ -96,6 +98,8 @@ void free_population(sim_ctx* ctx) {
   dfree(ctx->d_counters);
   dfree(ctx->d_scratch);
   dfree(ctx->d_lastnc);
+  dfree(ctx->d_order);
+  dfree(ctx->d_order_hist);
   dfree(ctx->d_stage);
   dfree(ctx->d_stage_st);
   ctx->n = 0;
@@ -160,10 +164,70 @@ struct LaunchArgs {
   Counters* counters;
   float* scratch;
   int* lastnc;
+  int* order;          // NULL: slot = packed index
+  unsigned* order_hist;
   int n;
   StepParams P;
   cudaStream_t stream;
 };
+
+// Slowest-first scheduling.  A launch lasts as long as its slowest robot, and
+// robots differ in cost by an order of magnitude (bodies, contacts, near
+// pairs), so before each launch the robots are bucketed by the SM cycles per
+// step they took in the previous launch (8 buckets per octave, descending) and
+// launched in that order: expensive robots start first and cheap ones fill
+// the SMs behind them (longest-processing-time-first list scheduling).  Only
+// the launch order changes; every robot's arithmetic is the same in any order.
+constexpr int kCostBuckets = 256;
+
+__device__ __forceinline__ int cost_bucket(float cycles_per_step) {
+  float c = cycles_per_step;
+  if (!(c >= 1.f)) c = 1.f;  // not yet measured, frozen, or not a number
+  if (c > 1e30f) c = 1e30f;
+  const int b = (int)(log2f(c) * 8.f);
+  return kCostBuckets - 1 - min(b, kCostBuckets - 1);
+}
+
+__global__ void cost_histogram(const float* __restrict__ scratch, int n, unsigned* __restrict__ hist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  atomicAdd(&hist[cost_bucket(scratch[(size_t)i * b3::kScratchFloats + b3::kDbgOffset + 31])], 1u);
+}
+
+// every block scans the (small) histogram itself, then places its robots
+__global__ void cost_scatter(const float* __restrict__ scratch, int n, unsigned* __restrict__ hist,
+                             int* __restrict__ order) {
+  __shared__ unsigned off[kCostBuckets];
+  if (threadIdx.x == 0) {
+    unsigned acc = 0;
+    for (int b = 0; b < kCostBuckets; ++b) {
+      off[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = cost_bucket(scratch[(size_t)i * b3::kScratchFloats + b3::kDbgOffset + 31]);
+  order[off[b] + atomicAdd(&hist[kCostBuckets + b], 1u)] = i;
+}
+
+// before the first launch: cost ~ bodies^2 (the launch order is then by size)
+__global__ void cost_init(const int4* __restrict__ meta, int n, float* __restrict__ scratch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float nb = (float)meta[i].x;
+  scratch[(size_t)i * b3::kScratchFloats + b3::kDbgOffset + 31] = 1000.f * nb * nb;
+}
+
+cudaError_t cost_order(const LaunchArgs& a) {
+  cudaError_t e = cudaMemsetAsync(a.order_hist, 0, 2 * kCostBuckets * sizeof(unsigned), a.stream);
+  if (e != cudaSuccess) return e;
+  const int nb = (a.n + 255) / 256;
+  cost_histogram<<<nb, 256, 0, a.stream>>>(a.scratch, a.n, a.order_hist);
+  cost_scatter<<<nb, 256, 0, a.stream>>>(a.scratch, a.n, a.order_hist, a.order);
+  return cudaGetLastError();
+}
 
 template <int WPB>
 cudaError_t launch_wpb(const LaunchArgs& a, int nsteps) {
@@ -176,7 +240,8 @@ cudaError_t launch_wpb(const LaunchArgs& a, int nsteps) {
   }
   dim3 grid((a.n + WPB - 1) / WPB), block(32 * WPB);
   b3::step_kernel<WPB><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s, a.status,
-                                                     a.counters, a.scratch, a.lastnc, a.n, nsteps, a.P);
+                                                     a.counters, a.scratch, a.lastnc, a.order, a.n, nsteps,
+                                                     a.P);
   return cudaGetLastError();
 }
 
@@ -192,6 +257,10 @@ cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb) {
 
 cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, int spl) {
   for (int done = 0; done < n_steps; done += spl) {
+    if (a.order) {
+      cudaError_t e = cost_order(a);
+      if (e != cudaSuccess) return e;
+    }
     cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb);
     if (e != cudaSuccess) return e;
   }
@@ -199,9 +268,9 @@ cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, int spl)
 }
 
 LaunchArgs ctx_args(sim_ctx* ctx) {
-  return LaunchArgs{ctx->d_mf,     ctx->d_mi,       ctx->d_meta,    ctx->d_pairs, ctx->d_q,
-                    ctx->d_v,      ctx->d_s,        ctx->d_status,  ctx->d_counters, ctx->d_scratch,
-                    ctx->d_lastnc, ctx->n,          ctx->P,         ctx->stream};
+  return LaunchArgs{ctx->d_mf,     ctx->d_mi,    ctx->d_meta,   ctx->d_pairs,       ctx->d_q,
+                    ctx->d_v,      ctx->d_s,     ctx->d_status, ctx->d_counters,    ctx->d_scratch,
+                    ctx->d_lastnc, ctx->d_order, ctx->d_order_hist, ctx->n, ctx->P, ctx->stream};
 }
 
 cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, int spl) {
@@ -336,7 +405,7 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
   if (e == cudaSuccess) {
     LaunchArgs args{pop->model_f, pop->model_i, reinterpret_cast<const int4*>(pop->meta), pop->pairs,
                     pop->q,       pop->v,       pop->cpg, pop->status, a.counters, a.scratch, a.lastnc,
-                    pop->n,       make_params(cfg), stream};
+                    nullptr,      nullptr,      pop->n,   make_params(cfg), stream};
     const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
     const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : 500;
     e = enqueue_launches(args, n_steps, wpb, spl);
@@ -521,6 +590,8 @@ int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
   ALLOC(ctx->d_counters, N * sizeof(Counters));
   ALLOC(ctx->d_scratch, N * b3::kScratchFloats * sizeof(float));
   ALLOC(ctx->d_lastnc, N * sizeof(int));
+  ALLOC(ctx->d_order, N * sizeof(int));
+  ALLOC(ctx->d_order_hist, 2 * kCostBuckets * sizeof(unsigned));
   ALLOC(ctx->d_stage, N * (SIM_QW + SIM_VW + SIM_SW) * sizeof(float));
   ALLOC(ctx->d_stage_st, N * sizeof(unsigned));
 #undef ALLOC
@@ -537,6 +608,10 @@ int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
   CK(cudaMemsetAsync(ctx->d_status, 0, N * sizeof(unsigned), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_counters, 0, N * sizeof(Counters), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_lastnc, 0, N * sizeof(int), ctx->stream));
+  // zero scratch, then the size-based cost estimate the first launch is ordered by
+  CK(cudaMemsetAsync(ctx->d_scratch, 0, N * b3::kScratchFloats * sizeof(float), ctx->stream));
+  cost_init<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_meta, n, ctx->d_scratch);
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
   return SIM_OK;
 }

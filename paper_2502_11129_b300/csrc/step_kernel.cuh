@@ -62,13 +62,15 @@ struct StepParams {
 };
 
 // global scratch per variant: candidate rows, the narrow phase's per-lane
-// staging rows, Y rows (32 floats each), the
-// Gauss-Seidel constants of each contact (12 floats), then the last step's
-// v_free and impulses (inspection only)
+// staging rows, Y rows (32 floats each), the Gauss-Seidel constants of each
+// contact (kCstW floats: b, 1/(A+R), R of its three rows, then the
+// normal-tangent couplings A_t1n, A_t2n), then the last step's v_free and
+// impulses (inspection only)
 constexpr size_t kStageOffset = (size_t)kCand * kCandW;            // 32 lanes x 8 points x 8 floats
 constexpr size_t kYOffset = kStageOffset + (size_t)32 * 8 * kCandW;
 constexpr size_t kCstOffset = kYOffset + (size_t)kYRows * 32;
-constexpr size_t kDbgOffset = kCstOffset + (size_t)kCapMax * 12;
+constexpr int kCstW = 12;        // Gauss-Seidel constants per contact (floats)
+constexpr size_t kDbgOffset = kCstOffset + (size_t)kCapMax * kCstW;
 constexpr int kPhases = 10;  // per-phase cycle counters (inspection only)
 constexpr size_t kScratchFloats = kDbgOffset + 32 + 4 * kCapMax + 16;
 
@@ -392,17 +394,27 @@ struct Counters {
   unsigned long long contacts, narrow, broad, steps, cycles;
 };
 
+// resident warps per SM the register budget is sized for (65536 / (32 x warps)
+// registers per thread)
+#ifndef B3_WARPS_PER_SM
+#define B3_WARPS_PER_SM 16
+#endif
+constexpr int kWarpsPerSM = B3_WARPS_PER_SM;
+
 template <int WPB>
-__global__ void __launch_bounds__(WPB * 32, 16 / WPB)
+__global__ void __launch_bounds__(WPB * 32, kWarpsPerSM / WPB)
 step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4* __restrict__ meta,
             const uint16_t* __restrict__ pairs, float* __restrict__ qg, float* __restrict__ vg,
             float* __restrict__ sg, unsigned* __restrict__ status, Counters* __restrict__ counters,
-            float* __restrict__ scratch, int* __restrict__ last_nc, int nvar, int nsteps, StepParams P) {
+            float* __restrict__ scratch, int* __restrict__ last_nc, const int* __restrict__ order, int nvar,
+            int nsteps, StepParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int var = blockIdx.x * WPB + wib;
-  if (var >= nvar) return;
+  const int slot = blockIdx.x * WPB + wib;
+  if (slot >= nvar) return;
+  // launch slot -> variant: slowest-first order when given (see cost_order)
+  const int var = order ? __ldg(order + slot) : slot;
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[wib];
 
   const int4 md = meta[var];
@@ -930,7 +942,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
         // penetration recovery speed, capped (ODE's maximum correcting velocity)
         const float bias = dir == 0 ? jv - fminf(P.erp * depth_k / dt, P.max_correct_vel) : jv;
-        float* cs = cstg + (size_t)k * 12 + 3 * dir;
+        float* cs = cstg + (size_t)k * kCstW + 3 * dir;
         cs[0] = bias;
         cs[1] = inv;
         cs[2] = Rr;
@@ -952,7 +964,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           a1 += p4.x * n4.x + p4.y * n4.y + p4.z * n4.z + p4.w * n4.w;
           a2 += q4.x * n4.x + q4.y * n4.y + q4.z * n4.z + q4.w * n4.w;
         }
-        float* cs = cstg + (size_t)k * 12;
+        float* cs = cstg + (size_t)k * kCstW;
         cs[9] = a1;
         cs[10] = a2;
         cs[11] = 0.f;
@@ -1014,11 +1026,9 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           float l2t = l2 - g2 * cb4.w;
           const float lim = P.mu * lnn;
           const float nt2 = l1t * l1t + l2t * l2t;
-          if (nt2 > lim * lim) {
-            const float sc = lim * rsqrtf(nt2);
-            l1t *= sc;
-            l2t *= sc;
-          }
+          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+          l1t *= sc;
+          l2t *= sc;
           w += an * dn + a1 * (l1t - l1) + a2 * (l2t - l2);
           lam = lane == r ? lnn : (lane == r + 1 ? l1t : (lane == r + 2 ? l2t : lam));
           an = nan0; a1 = na1; a2 = na2;
@@ -1032,8 +1042,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     } else if (nc > 0) {
       // dof space (lane = dof, u = L^T (v - v_free)); the impulses of contact
       // k live in lane k & 31 (slot k >> 5)
-      float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
       const float4* c4 = reinterpret_cast<const float4*>(cstg);
+      float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
       float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
       for (int it = 0; it < P.iters; ++it) {
         for (int k = 0; k < nc; ++k) {
@@ -1059,16 +1069,17 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           float l2t = l2 - g2 * cb4.w;
           const float lim = P.mu * lnn;
           const float nt2 = l1t * l1t + l2t * l2t;
-          if (nt2 > lim * lim) {
-            const float sc = lim * rsqrtf(nt2);
-            l1t *= sc;
-            l2t *= sc;
-          }
+          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+          l1t *= sc;
+          l2t *= sc;
           u += y0 * dn + y1 * (l1t - l1) + y2 * (l2t - l2);
-          if (lane == src) {
-            if (hi) { lam_b[0] = lnn; lam_b[1] = l1t; lam_b[2] = l2t; }
-            else { lam_a[0] = lnn; lam_a[1] = l1t; lam_a[2] = l2t; }
-          }
+          const bool mine_a = lane == src && !hi, mine_b = lane == src && hi;
+          lam_a[0] = mine_a ? lnn : lam_a[0];
+          lam_a[1] = mine_a ? l1t : lam_a[1];
+          lam_a[2] = mine_a ? l2t : lam_a[2];
+          lam_b[0] = mine_b ? lnn : lam_b[0];
+          lam_b[1] = mine_b ? l1t : lam_b[1];
+          lam_b[2] = mine_b ? l2t : lam_b[2];
           y0 = ny0; y1 = ny1; y2 = ny2;
           ca = na; cb4 = nb4; cc4 = nc4;
         }
