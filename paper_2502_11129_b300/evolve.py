@@ -29,12 +29,19 @@ import time
 import numpy as np
 
 from . import population as P
+from . import shard as SH
 from . import sim as S
 from . import surrogate as SG
 
+# process group when launched with one process per GPU (torchrun); every rank
+# runs the same EA loop with the same seeds and simulates its shard of each
+# population (see shard.py)
+_DIST = None
+_DEVICE = 0
 
-def simulate(pop: P.Population, steps: int, **cfg) -> np.ndarray:
-    """Core xy displacement of every robot after `steps` steps from rest."""
+
+def _simulate_local(pop: P.Population, steps: int, **cfg) -> np.ndarray:
+    cfg.setdefault("device", _DEVICE)
     sm = S.Sim(**cfg)
     try:
         sm.set_population(pop)
@@ -47,6 +54,12 @@ def simulate(pop: P.Population, steps: int, **cfg) -> np.ndarray:
         return f.astype(np.float64)
     finally:
         sm.close()
+
+
+def simulate(pop: P.Population, steps: int, **cfg) -> np.ndarray:
+    """Core xy displacement of every robot after `steps` steps from rest
+    (sharded over the ranks of the process group, if there is one)."""
+    return SH.run_sharded(pop, lambda sub: _simulate_local(sub, steps, **cfg), _DIST)
 
 
 def ranks(a):
@@ -98,7 +111,7 @@ def screening(n_train=50000, n_screen=65536, k=4096, steps=5000, epochs=30, batc
     train = P.grammar(n_train, seed=seed)
     f_train = simulate(train, steps)
     t_sim = time.perf_counter() - t0
-    sur = SG.Surrogate(seed=seed)
+    sur = SG.Surrogate(seed=seed, device=_DEVICE)
     X = sur.encode(train)
     t1 = time.perf_counter()
     loss = sur.train(X, f_train.astype(np.float32), epochs=epochs, batch=batch)
@@ -155,7 +168,7 @@ def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=Fa
     rng = np.random.default_rng(seed)
     morphs = P.grammar(n_morph, seed=seed)
     best_f = simulate(morphs, steps)
-    sur = SG.Surrogate(seed=seed) if surrogate else None
+    sur = SG.Surrogate(seed=seed, device=_DEVICE) if surrogate else None
     data_X = [sur.encode(morphs)] if surrogate else []
     data_y = [best_f.copy()]
     trace = RunLog([float(best_f.max())], [n_morph], [n_morph], [0.0])
@@ -231,7 +244,22 @@ def _concat(a: P.Population, b: P.Population) -> P.Population:
     return P.Population(**fields)
 
 
+def _init_dist():
+    """One process per GPU under torchrun: device = LOCAL_RANK."""
+    global _DIST, _DEVICE
+    import os
+    if int(os.environ.get("WORLD_SIZE", "1")) <= 1:
+        return 0
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend="gloo")
+    _DIST = dist
+    _DEVICE = int(os.environ.get("LOCAL_RANK", "0"))
+    return _DEVICE
+
+
 def main():
+    _init_dist()
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", choices=["screening", "memetic"], default="screening")
     ap.add_argument("--n-train", type=int, default=50000)
@@ -246,14 +274,18 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--full-eval", action="store_true")
     a = ap.parse_args()
+    lead = _DIST is None or _DIST.get_rank() == 0
+    say = print if lead else (lambda *args, **kw: None)
     if a.mode == "screening":
-        print(json.dumps(screening(a.n_train, a.n_screen, a.k, a.steps, a.epochs, seed=a.seed,
-                                   full_eval=a.full_eval)))
+        out = screening(a.n_train, a.n_screen, a.k, a.steps, a.epochs, seed=a.seed, full_eval=a.full_eval)
     else:
-        plain = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=False, seed=a.seed)
+        plain = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=False, seed=a.seed, log=say)
         sur = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=True, screen_factor=a.screen_factor,
-                      seed=a.seed, target=plain["final_best"])
-        print(json.dumps(dict(plain=plain, surrogate=sur)))
+                      seed=a.seed, target=plain["final_best"], log=say)
+        out = dict(plain=plain, surrogate=sur)
+    say(json.dumps(out))
+    if _DIST is not None:
+        _DIST.destroy_process_group()
 
 
 if __name__ == "__main__":
