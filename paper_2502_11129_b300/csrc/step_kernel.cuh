@@ -299,22 +299,26 @@ __device__ __noinline__ int box_box_lane(const WarpSmem& sm, const float* __rest
     const float s1[4] = {1.f, -1.f, -1.f, 1.f}, s2[4] = {1.f, 1.f, -1.f, -1.f};
     float poly[2][8][3];
     int np = 4, cur = 0;
+#pragma unroll 1
     for (int v = 0; v < 4; ++v)
       for (int k = 0; k < 3; ++k)
         poly[0][v][k] = fc[k] + s1[v] * hI[k1] * Ix[k1][k] + s2[v] * hI[k2] * Ix[k2][k];
     int u1 = (ri + 1) % 3, u2 = (ri + 2) % 3;
     if (u1 > u2) { const int t = u1; u1 = u2; u2 = t; }
+#pragma unroll 1
     for (int pl = 0; pl < 4 && np > 0; ++pl) {
       const int ax = pl < 2 ? u1 : u2;
       const float ps = (pl & 1) ? -1.f : 1.f;
       const float u[3] = {Rx[ax][0], Rx[ax][1], Rx[ax][2]};
       const float eh = hR[ax];
       float dist[8];
+#pragma unroll 1
       for (int v = 0; v < np; ++v) {
         const float rel[3] = {poly[cur][v][0] - cR[0], poly[cur][v][1] - cR[1], poly[cur][v][2] - cR[2]};
         dist[v] = ps * dot3(rel, u) - eh;
       }
       int no = 0;
+#pragma unroll 1
       for (int v = 0; v < np; ++v) {
         const int nx = (v + 1) % np;
         const bool in_v = dist[v] <= 0.f, in_n = dist[nx] <= 0.f;
@@ -334,6 +338,7 @@ __device__ __noinline__ int box_box_lane(const WarpSmem& sm, const float* __rest
       cur ^= 1;
     }
     int n = 0;
+#pragma unroll 1
     for (int v = 0; v < np; ++v) {
       const float rel[3] = {poly[cur][v][0] - cR[0], poly[cur][v][1] - cR[1], poly[cur][v][2] - cR[2]};
       const float depth = hR[ri] - dot3(rel, nref);
