@@ -96,6 +96,11 @@ typedef struct {
     uint64_t stream;          /* cudaStream_t or 0                           */
     int32_t steps_per_launch; /* persistent chunk; 0: library default        */
     int32_t warps_per_block;  /* 0: autotuned default                        */
+    int32_t phase_lock;       /* 1: the warps of a block pass the step's phase
+                                 boundaries together (block barriers: fewer
+                                 distinct phases per SM at a time, but every
+                                 phase waits for the block's slowest robot);
+                                 0: off (default)                           */
 } sim_config;
 
 /* Model of one variant.  Arrays have n_bodies entries (per body) unless
@@ -182,6 +187,12 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
  * integration, unused).  Synchronises. */
 int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out,
                      float* cycles_per_step);
+
+/* Host evaluation of the step kernel's FP64 sine / cosine routine (the one
+ * that the hinge angles go through on the device, compiled here for the
+ * host): s[i], c[i] for x[i], i < n.  Inspection and testing only; no device
+ * work, no context needed.  SIM_EINVAL for NULL arrays or n < 0. */
+int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
 
 /* ---- Stepping without any allocation --------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

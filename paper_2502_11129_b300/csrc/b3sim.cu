@@ -53,6 +53,7 @@ struct sim_ctx {
   StepParams P{};
   int steps_per_launch = 500;
   int wpb = 4;
+  bool lock = false;  // phase-locked launches (warps of a block in step)
   std::map<long long, cudaGraphExec_t> graphs;
 };
 
@@ -229,39 +230,41 @@ cudaError_t cost_order(const LaunchArgs& a) {
   return cudaGetLastError();
 }
 
-template <int WPB>
+template <int WPB, bool LOCK>
 cudaError_t launch_wpb(const LaunchArgs& a, int nsteps) {
   const size_t sm = smem_bytes(WPB);
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(b3::step_kernel<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(b3::step_kernel<WPB, LOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   dim3 grid((a.n + WPB - 1) / WPB), block(32 * WPB);
-  b3::step_kernel<WPB><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s, a.status,
-                                                     a.counters, a.scratch, a.lastnc, a.order, a.n, nsteps,
-                                                     a.P);
+  b3::step_kernel<WPB, LOCK><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s, a.status,
+                                                           a.counters, a.scratch, a.lastnc, a.order, a.n, nsteps,
+                                                           a.P);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb) {
+// phase locking needs a block of several warps; with one warp it is a no-op
+cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb, bool lock) {
   switch (wpb) {
-    case 1: return launch_wpb<1>(a, nsteps);
-    case 2: return launch_wpb<2>(a, nsteps);
-    case 4: return launch_wpb<4>(a, nsteps);
-    case 8: return launch_wpb<8>(a, nsteps);
+    case 1: return launch_wpb<1, false>(a, nsteps);
+    case 2: return lock ? launch_wpb<2, true>(a, nsteps) : launch_wpb<2, false>(a, nsteps);
+    case 4: return lock ? launch_wpb<4, true>(a, nsteps) : launch_wpb<4, false>(a, nsteps);
+    case 8: return lock ? launch_wpb<8, true>(a, nsteps) : launch_wpb<8, false>(a, nsteps);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, int spl) {
+cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool lock, int spl) {
   for (int done = 0; done < n_steps; done += spl) {
     if (a.order) {
       cudaError_t e = cost_order(a);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb);
+    cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb, lock);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -273,8 +276,8 @@ LaunchArgs ctx_args(sim_ctx* ctx) {
                     ctx->d_lastnc, ctx->d_order, ctx->d_order_hist, ctx->n, ctx->P, ctx->stream};
 }
 
-cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, int spl) {
-  return enqueue_launches(ctx_args(ctx), n_steps, wpb, spl);
+cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int spl) {
+  return enqueue_launches(ctx_args(ctx), n_steps, wpb, lock, spl);
 }
 
 bool config_ok(const sim_config* cfg) {
@@ -282,7 +285,8 @@ bool config_ok(const sim_config* cfg) {
          cfg->contact_cap <= SIM_MAX_CONTACT_CAP && cfg->soft_tau > 0.f && cfg->soft_zeta >= 0.f &&
          cfg->mu >= 0.f && cfg->steps_per_launch >= 0 && cfg->max_correct_vel > 0.f &&
          (cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
-          cfg->warps_per_block == 4 || cfg->warps_per_block == 8);
+          cfg->warps_per_block == 4 || cfg->warps_per_block == 8) &&
+         (cfg->phase_lock == 0 || cfg->phase_lock == 1);
 }
 
 // FP32 step constants from a configuration (ERP / CFM of the soft contacts
@@ -361,6 +365,12 @@ cudaError_t noalloc_setup(int dev, NoallocAddrs* out) {
 
 extern "C" {
 
+int sim_debug_sincos(const double* x, int32_t n, double* s, double* c) {
+  if (!x || !s || !c || n < 0) return SIM_EINVAL;
+  for (int32_t i = 0; i < n; ++i) b3::sincos_f64(x[i], &s[i], &c[i]);
+  return SIM_OK;
+}
+
 int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, int32_t n_steps) {
   if (!cfg || !pop) {
     g_create_error = "sim_step_n_noalloc: cfg or pop is NULL";
@@ -408,7 +418,7 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
                     nullptr,      nullptr,      pop->n,   make_params(cfg), stream};
     const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
     const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : 500;
-    e = enqueue_launches(args, n_steps, wpb, spl);
+    e = enqueue_launches(args, n_steps, wpb, cfg->phase_lock == 1, spl);
   }
   if (e != cudaSuccess) {
     g_create_error_buf = std::string("sim_step_n_noalloc: ") + cudaGetErrorString(e);
@@ -455,6 +465,7 @@ int sim_create(const sim_config* cfg, sim_ctx_t** out) {
   ctx->P = make_params(cfg);
   if (cfg->steps_per_launch > 0) ctx->steps_per_launch = cfg->steps_per_launch;
   if (cfg->warps_per_block > 0) ctx->wpb = cfg->warps_per_block;
+  ctx->lock = cfg->phase_lock == 1;
   *out = ctx;
   return SIM_OK;
 }
@@ -643,12 +654,12 @@ int sim_step_n(sim_ctx_t* ctx, int32_t n_steps) {
   if (n_steps < 0) return fail(ctx, SIM_EINVAL, "sim_step_n: n_steps < 0");
   if (n_steps == 0) return SIM_OK;
   CK(cudaSetDevice(ctx->cfg.device));
-  const long long key = ((long long)n_steps << 8) | ctx->wpb;
+  const long long key = ((long long)n_steps << 8) | (ctx->lock ? 16 : 0) | ctx->wpb;
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = enqueue_steps(ctx, n_steps, ctx->wpb, ctx->steps_per_launch);
+    cudaError_t le = enqueue_steps(ctx, n_steps, ctx->wpb, ctx->lock, ctx->steps_per_launch);
     cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
     if (le != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -729,17 +740,21 @@ int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // warps per block; the phase lock stays as configured: a short probe
+  // from one state does not show its cost in later steps, where the
+  // slowest robot of a block sets the pace of every phase boundary
   const int cands[4] = {1, 2, 4, 8};
   float best_ms = 1e30f;
   int best = ctx->wpb;
-  for (int c : cands) {
+  for (const int c : cands) {
+    const bool lk = ctx->lock;
     cudaError_t e = restore();
     if (e != cudaSuccess) break;
-    e = enqueue_steps(ctx, probe_steps, c, probe_steps);  // warm-up (and attribute set-up)
+    e = enqueue_steps(ctx, probe_steps, c, lk, probe_steps);  // warm-up (and attribute set-up)
     if (e != cudaSuccess) continue;
     restore();
     cudaEventRecord(e0, ctx->stream);
-    e = enqueue_steps(ctx, probe_steps, c, probe_steps);
+    e = enqueue_steps(ctx, probe_steps, c, lk, probe_steps);
     cudaEventRecord(e1, ctx->stream);
     if (cudaEventSynchronize(e1) != cudaSuccess || e != cudaSuccess) continue;
     float ms = 0.f;

@@ -386,6 +386,45 @@ __device__ __noinline__ int box_box_lane(const WarpSmem& sm, const float* __rest
   return 1;
 }
 
+// Double-precision sine and cosine of one argument, compact enough to live in
+// the step loop: Cody & Waite (1980) reduction x = k pi/2 + r with pi/2 split
+// into a 33-bit head (k * head is exact for |k| < 2^20) and a double tail,
+// then the Taylor series of sin and cos on |r| <= pi/4 through r^17 and r^18
+// (truncation below 1e-19), and the quadrant swap.  Good to a few ulp for
+// |x| < 1e6, far beyond any hinge angle.
+__host__ __device__ __forceinline__ void sincos_f64(double x, double* s_out, double* c_out) {
+  constexpr double kTwoOverPi = 0.63661977236758138;
+  constexpr double kPio2Hi = 1.5707963267341256;     // pi/2 to 33 bits
+  constexpr double kPio2Lo = 6.077100506506192e-11;  // pi/2 - kPio2Hi
+  const double k = rint(x * kTwoOverPi);
+  const double r = (x - k * kPio2Hi) - k * kPio2Lo;
+  const double z = r * r;
+  // 1/n! for the odd (sin) and even (cos) Taylor terms
+  double ps = 1.0 / 355687428096000.0;                 // 1/17!
+  ps = ps * z - 1.0 / 1307674368000.0;                 // 1/15!
+  ps = ps * z + 1.0 / 6227020800.0;                    // 1/13!
+  ps = ps * z - 1.0 / 39916800.0;                      // 1/11!
+  ps = ps * z + 1.0 / 362880.0;                        // 1/9!
+  ps = ps * z - 1.0 / 5040.0;                          // 1/7!
+  ps = ps * z + 1.0 / 120.0;                           // 1/5!
+  ps = ps * z - 1.0 / 6.0;                             // 1/3!
+  const double sr = r + r * z * ps;
+  double pc = -1.0 / 6402373705728000.0;               // 1/18!
+  pc = pc * z + 1.0 / 20922789888000.0;                // 1/16!
+  pc = pc * z - 1.0 / 87178291200.0;                   // 1/14!
+  pc = pc * z + 1.0 / 479001600.0;                     // 1/12!
+  pc = pc * z - 1.0 / 3628800.0;                       // 1/10!
+  pc = pc * z + 1.0 / 40320.0;                         // 1/8!
+  pc = pc * z - 1.0 / 720.0;                           // 1/6!
+  pc = pc * z + 1.0 / 24.0;                            // 1/4!
+  pc = pc * z - 0.5;                                   // 1/2!
+  const double cr = 1.0 + z * pc;
+  const int q = (int)((long long)k & 3);
+  const double sa = (q & 1) ? cr : sr, ca = (q & 1) ? sr : cr;
+  *s_out = (q & 2) ? -sa : sa;
+  *c_out = ((q + 1) & 2) ? -ca : ca;
+}
+
 // Duff et al. 2017 ("Building an Orthonormal Basis, Revisited"), JCGT 6(1)
 __device__ __forceinline__ void tangent_basis(const float* n, float* t1, float* t2) {
   float s = n[2] >= 0.f ? 1.f : -1.f;
@@ -406,7 +445,13 @@ struct Counters {
 #endif
 constexpr int kWarpsPerSM = B3_WARPS_PER_SM;
 
-template <int WPB>
+// Block barriers per step of a phase-locked launch (LOCK): the warps of a
+// block pass every phase boundary together, so that the SM runs few distinct
+// phases at a time (instruction-cache locality) at the cost of waiting for the
+// block's slowest robot at each boundary.
+constexpr int kLockBarriers = 5;
+
+template <int WPB, bool LOCK>
 __global__ void __launch_bounds__(WPB * 32, kWarpsPerSM / WPB)
 step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4* __restrict__ meta,
             const uint16_t* __restrict__ pairs, float* __restrict__ qg, float* __restrict__ vg,
@@ -417,7 +462,14 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int slot = blockIdx.x * WPB + wib;
-  if (slot >= nvar) return;
+  if (slot >= nvar) {
+    if constexpr (LOCK) {
+      // a warp without a robot still takes every block barrier of every step
+      for (int step = 0; step < nsteps; ++step)
+        for (int b = 0; b < kLockBarriers; ++b) __syncthreads();
+    }
+    return;
+  }
   // launch slot -> variant: slowest-first order when given (see cost_order)
   const int var = order ? __ldg(order + slot) : slot;
   WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[wib];
@@ -469,13 +521,25 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     if (lane == 0) sm.ph[i] += (unsigned long long)(t_ - tph);       \
     tph = t_;                                                        \
   } while (0)
+#define B3_LOCK()                \
+  do {                           \
+    if constexpr (LOCK) {        \
+      __syncwarp();              \
+      __syncthreads();           \
+    }                            \
+  } while (0)
   float* cand = scratch + (size_t)var * kScratchFloats;
   float* Yg = cand + kYOffset;
   float* cstg = cand + kCstOffset;
   __syncwarp();
 
   for (int step = 0; step < nsteps; ++step) {
-    if (st & 5u) break;  // frozen (non-finite state or failed factorisation)
+    // frozen (non-finite state or failed factorisation): stop, or under LOCK
+    // keep computing on the frozen state without committing it, so that every
+    // warp takes the same barriers
+    if constexpr (!LOCK) {
+      if (st & 5u) break;
+    }
     const float dt = P.dt;
 
     // ---------------- 1. CPG and PD torque (lane = body / hinge)
@@ -505,8 +569,11 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     float R0[9];
     quat_to_R(qw, qx, qy, qz, R0);
     float R[9], r[3] = {0.f, 0.f, 0.f};
-    float sth, cth;
-    sincosf(theta, &sth, &cth);
+    // hinge angle sine and cosine in FP64 (the height chain below needs them
+    // there); the FP32 kinematics use them rounded
+    double sd, cd;
+    sincos_f64((double)theta, &sd, &cd);
+    const float sth = (float)sd, cth = (float)cd;
     {
       float Rl[9];
       const int k = axis, i = (axis + 1) % 3, j = (axis + 2) % 3;
@@ -548,8 +615,6 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       hz0 = 2.0 * (dx * dz - dw * dy);
       hz1 = 2.0 * (dy * dz + dw * dx);
       hz2 = 1.0 - 2.0 * (dx * dx + dy * dy);
-      double sd, cd;
-      sincos((double)theta, &sd, &cd);
       const int k = axis, i = (axis + 1) % 3, j = (axis + 2) % 3;
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
         const double p0 = __shfl_sync(kFull, hz0, par0), p1 = __shfl_sync(kFull, hz1, par0);
@@ -715,29 +780,42 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     __syncwarp();
 
     B3_PHASE(1);
-    // ---------------- 5. Cholesky (right-looking, lane = row) and v_free
+    B3_LOCK();
+    // ---------------- 5. Cholesky (left-looking, lane = row) and v_free
+    // Column j: every row i >= j forms s_i = sum_{k<j} L_ik L_jk from its own
+    // finished row and the broadcast row j (independent loads, no
+    // read-modify-write chain through shared memory); lane j turns its value
+    // into the pivot, the rows below divide by it.
     bool chol_ok = true;
     {
-      const int tl = tri(lane);
-      for (int k = 0; k < nv; ++k) {
-        const float dkk = sm.M[tri(k) + k];
-        if (!(dkk > 0.f)) { chol_ok = false; break; }
-        const float d = sqrtf(dkk);
-        const float inv = 1.f / d;
-        float lik = 0.f;
-        if (lane > k && lane < nv) lik = sm.M[tl + k] * inv;
-        __syncwarp();
-        if (lane == k) { sm.M[tl + k] = d; sm.invd[k] = inv; }
-        if (lane > k && lane < nv) sm.M[tl + k] = lik;
-        __syncwarp();
-        for (int j = k + 1; j < nv; ++j) {
-          const float ljk = sm.M[tri(j) + k];
-          if (lane >= j && lane < nv) sm.M[tl + j] -= lik * ljk;
+      const float* Li = sm.M + tri(lane);
+      const bool row = lane < nv;
+      for (int j = 0; j < nv; ++j) {
+        const float* Lj = sm.M + tri(j);
+        float s0 = 0.f, s1 = 0.f;
+        if (row && lane >= j) {
+          int k = 0;
+#pragma unroll 1
+          for (; k + 1 < j; k += 2) {
+            s0 += Li[k] * Lj[k];
+            s1 += Li[k + 1] * Lj[k + 1];
+          }
+          if (k < j) s0 += Li[k] * Lj[k];
         }
+        const float mij = (row && lane >= j) ? Li[j] - (s0 + s1) : 0.f;
+        const float piv = shf(mij, j);
+        if (!(piv > 0.f)) { chol_ok = false; break; }
+        const float d = sqrtf(piv);
+        const float inv = 1.f / d;
+        if (lane == j) { sm.M[tri(j) + j] = d; sm.invd[j] = inv; }
+        if (row && lane > j) sm.M[tri(lane) + j] = mij * inv;
         __syncwarp();
       }
     }
-    if (!chol_ok) { st |= 4u; break; }
+    if (!chol_ok) {
+      st |= 4u;
+      if constexpr (!LOCK) break;
+    }
     float vfree;
     {
       float y = lower_solve(sm, tau_d - c_d, nv, lane);
@@ -748,6 +826,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     }
 
     B3_PHASE(2);
+    B3_LOCK();
     // ---------------- 6. contact candidates
     int ncand = 0;
     if (P.ground) {
@@ -875,6 +954,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     __syncwarp();
 
     B3_PHASE(5);
+    B3_LOCK();
     // ---------------- 7. contact rows: Y_r = L^-1 J_r^T and Gauss-Seidel constants (lane = row)
     float w_row = 0.f;  // with at most 32 rows: this lane's row residual J_r v_free - bias
     for (int r0 = 0; r0 < 3 * nc; r0 += 32) {
@@ -980,6 +1060,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     __syncwarp();
 
     B3_PHASE(6);
+    B3_LOCK();
     // ---------------- 8. soft projected Gauss-Seidel
     float u = 0.f;
     if (nc > 0 && 3 * nc <= 32) {
@@ -1094,6 +1175,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     if (lane >= nv) vplus = 0.f;
 
     B3_PHASE(7);
+    B3_LOCK();
     // ---------------- 9. semi-implicit Euler
     const float vx = shf(vplus, 0), vy = shf(vplus, 1), vz = shf(vplus, 2);
     const float ox = shf(vplus, 3), oy = shf(vplus, 4), oz = shf(vplus, 5);
@@ -1119,16 +1201,22 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     bool bad = !(isfinite(np0x) && isfinite(np0y) && isfinite(np0z) && isfinite(r0) && isfinite(r1) &&
                  isfinite(r2) && isfinite(r3));
     bad = bad || !isfinite(ntheta) || !isfinite(vplus) || !isfinite(xn) || !isfinite(yn);
-    if (__any_sync(kFull, bad)) { st |= 1u; break; }
-    p0x = np0x; p0y = np0y; p0z = np0z;
-    qw = r0; qx = r1; qy = r2; qz = r3;
-    theta = ntheta;
-    vd = vplus;
-    xo = xn; yo = yn;
-    ++n_steps;
+    if (__any_sync(kFull, bad)) {
+      st |= 1u;
+      if constexpr (!LOCK) break;
+    }
+    if (!(st & 5u)) {
+      p0x = np0x; p0y = np0y; p0z = np0z;
+      qw = r0; qx = r1; qy = r2; qz = r3;
+      theta = ntheta;
+      vd = vplus;
+      xo = xn; yo = yn;
+      ++n_steps;
+    }
     B3_PHASE(8);
   }
 #undef B3_PHASE
+#undef B3_LOCK
 
   // ---- write back
   __syncwarp();

@@ -25,7 +25,7 @@ STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: 
 
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
            "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
-           "sim_debug_contacts", "sim_debug_solver", "sim_step_n_noalloc", "sim_last_error"]
+           "sim_debug_contacts", "sim_debug_solver", "sim_debug_sincos", "sim_step_n_noalloc", "sim_last_error"]
 
 
 class SimConfig(C.Structure):
@@ -36,7 +36,7 @@ class SimConfig(C.Structure):
         ("tau_max", C.c_float), ("theta_max", C.c_float), ("armature", C.c_float),
         ("ground", C.c_int32), ("box_box", C.c_int32), ("actuate", C.c_int32),
         ("max_correct_vel", C.c_float), ("device", C.c_int32), ("stream", C.c_uint64), ("steps_per_launch", C.c_int32),
-        ("warps_per_block", C.c_int32),
+        ("warps_per_block", C.c_int32), ("phase_lock", C.c_int32),
     ]
 
 
@@ -65,7 +65,7 @@ class Counters(C.Structure):
 DEFAULTS = dict(dt=0.002, gravity=(0.0, 0.0, -9.81), pgs_iters=30, soft_tau=0.02, soft_zeta=1.0,
                 mu=1.0, contact_cap=64, kp=2.0, kd=0.05, tau_max=1.0, theta_max=np.pi / 2,
                 armature=1e-4, ground=1, box_box=1, actuate=1, max_correct_vel=0.1, device=0, stream=0,
-                steps_per_launch=0, warps_per_block=0)
+                steps_per_launch=0, warps_per_block=0, phase_lock=0)
 
 _lib = None
 
@@ -95,6 +95,7 @@ def lib():
         L.sim_debug_contacts.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, P(C.c_int32)]
         L.sim_debug_solver.argtypes = [vp, C.c_int32, vp, vp, P(C.c_int32), vp]
         L.sim_step_n_noalloc.argtypes = [P(SimConfig), P(DevicePopulation), C.c_int32]
+        L.sim_debug_sincos.argtypes = [vp, C.c_int32, vp, vp]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
@@ -264,3 +265,14 @@ class Sim:
                     "sim_debug_solver")
         return dict(vfree=vfree, lam=lam[:3 * n.value].reshape(-1, 3), n=n.value,
                     cycles_per_step=float(cyc[0]), phase_cycles=cyc[1:10].copy())
+
+
+def debug_sincos(x):
+    """The step kernel's FP64 sine / cosine routine evaluated on the host."""
+    x = np.ascontiguousarray(x, np.float64)
+    s = np.zeros_like(x)
+    c = np.zeros_like(x)
+    rc = lib().sim_debug_sincos(_ptr(x), x.size, _ptr(s), _ptr(c))
+    if rc != 0:
+        raise SimError(f"sim_debug_sincos: {rc}")
+    return s, c

@@ -8,6 +8,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2502_11129_b300 import build as B
@@ -77,3 +78,17 @@ def test_null_context_is_rejected():
     assert L.sim_step_n(None, 1) == -1
     assert L.sim_set_population(None, None, 0) == -1
     assert L.sim_read_state(None, 0, 0, None, None, None, None) == -1
+
+
+def test_step_kernel_fp64_sincos_against_libm():
+    """The hinge-angle sine / cosine routine of the step kernel (host build of
+    the same source) against the platform libm: absolute error within 4e-16
+    on |x| <= 10 and within 1e-15 on |x| <= 1e5."""
+    rng = np.random.default_rng(0)
+    for lim, tol in ((10.0, 4e-16), (1e5, 1e-15)):
+        x = np.concatenate([rng.uniform(-lim, lim, 200000), np.linspace(-lim, lim, 10001),
+                            np.pi / 2 * np.arange(-6, 7), [0.0, -0.0, 1e-300]])
+        s, c = S.debug_sincos(x)
+        assert np.abs(s - np.sin(x)).max() <= tol
+        assert np.abs(c - np.cos(x)).max() <= tol
+    assert S.lib().sim_debug_sincos(None, 1, None, None) == -1  # SIM_EINVAL

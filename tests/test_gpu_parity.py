@@ -274,3 +274,27 @@ def test_autotune_keeps_state():
     b.set_state(Q, V, Sx)
     b.step(30)
     assert np.array_equal(a.read_state()[0], b.read_state()[0])
+
+
+def test_launch_shapes_and_phase_lock_agree_bitwise():
+    """Warps per block, phase-locked blocks (with idle warps in the last
+    block and a frozen robot that keeps taking the barriers) and the
+    slowest-first launch order change only the schedule: every robot's state
+    is bitwise the same."""
+    pop = P.grammar(203, seed=47).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    V[5, 8] = np.nan  # robot 5 freezes at its first step
+    ref = None
+    for wpb, lock in ((1, 0), (2, 1), (4, 0), (4, 1), (8, 1)):
+        sm = _gpu_sim(pop, warps_per_block=wpb, phase_lock=lock, steps_per_launch=25)
+        sm.set_state(Q, V, Sx)
+        sm.step(60)
+        out = sm.read_state()
+        sm.close()
+        assert out[3][5] & S.ST_NONFINITE and np.array_equal(out[0][5], Q[5])
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref, out):
+                assert np.array_equal(a, b, equal_nan=True), (wpb, lock)
