@@ -348,7 +348,7 @@ def random_state(pop: Population, seed: int, angle=0.6, rate=1.0, lin=0.5, ang=0
     rng = np.random.default_rng(seed)
     q = pop.q0.copy()
     v = np.zeros_like(pop.v0)
-    s = np.zeros((pop.n, 2 * MAX_HINGES))
+    s = np.zeros((pop.n, 2 * (MAXB - 1)))
     for i in range(pop.n):
         nb = int(pop.nb[i])
         quat = rng.normal(size=4)
@@ -364,7 +364,7 @@ def random_state(pop: Population, seed: int, angle=0.6, rate=1.0, lin=0.5, ang=0
 
 def cpg_initial(pop: Population) -> np.ndarray:
     """Initial oscillator state: x = y = 1/sqrt(2) for every hinge."""
-    s = np.zeros((pop.n, 2 * MAX_HINGES))
+    s = np.zeros((pop.n, 2 * (MAXB - 1)))
     for i in range(pop.n):
         nh = int(pop.nb[i]) - 1
         s[i, : 2 * nh] = np.sqrt(0.5)

@@ -31,13 +31,9 @@ def test_libraries_build_and_export_every_declared_symbol():
     B.build()
     decl = header_functions()
     assert "b3sim.h" in decl and len(decl["b3sim.h"]) >= 11
-    libs = {"b3sim.h": S.LIB_PATH}
-    extra = {}
-    try:
-        from paper_2502_11129_b300 import surrogate as SG
-        libs["b3sur.h"] = SG.LIB_PATH
-    except ImportError:
-        pass
+    from paper_2502_11129_b300 import cpu as CP
+    from paper_2502_11129_b300 import surrogate as SG
+    libs = {"b3sim.h": S.LIB_PATH, "b3sur.h": SG.LIB_PATH, "b3cpu.h": CP.LIB_PATH}
     for header, names in decl.items():
         assert header in libs, f"no library for {header}"
         L = C.CDLL(libs[header])
@@ -46,10 +42,12 @@ def test_libraries_build_and_export_every_declared_symbol():
 
 
 def test_binding_lists_every_declared_entry_point():
+    from paper_2502_11129_b300 import cpu as CP
     from paper_2502_11129_b300 import surrogate as SG
     decl = header_functions()
     assert sorted(decl["b3sim.h"]) == sorted(S.EXPORTS)
     assert sorted(decl["b3sur.h"]) == sorted(SG.EXPORTS)
+    assert sorted(decl["b3cpu.h"]) == sorted(CP.EXPORTS)
 
 
 def test_sim_create_argument_errors_without_device():

@@ -1,0 +1,169 @@
+"""Host (CPU) engine (libb3cpu, the CPU side of the hybrid allocation) vs the
+FP64 oracle, and the hybrid allocation logic -- all on the CPU.
+
+Same bars as the GPU path (tests/test_gpu_parity.py): one step from identical
+FP32-rounded states within 1e-5 relative per variant (velocity scaled by
+max(|v+|, |v_free|, 1)), robots with a discrete decision within 1e-5 of its
+threshold in the oracle reported separately; contact-free flight within
+1e-4 m over 200 steps.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2502_11129_b300 import cpu as CP
+from paper_2502_11129_b300 import hybrid as H
+from paper_2502_11129_b300 import population as P
+from paper_2502_11129_b300 import sim as S
+
+TOL = 1e-5
+
+
+def oracle():
+    from oracle import oracle as O
+    return O
+
+
+def _one_step(pop, q, v, s, **cfg):
+    O = oracle()
+    pop32 = pop.as_float32()
+    Q, V, Sx = S.state_rows(pop32, q, v, s)
+    cs = CP.CpuSim(**cfg)
+    cs.set_population(pop32)
+    cs.set_state(Q, V, Sx)
+    cs.step(1)
+    gq, gv, gs, gst = cs.read_state()
+    cs.close()
+    keep = {k: val for k, val in cfg.items() if k in ("contact_cap", "box_box", "ground", "actuate")}
+    prm = O.default_params(**keep)
+    errs = np.zeros((pop.n, 3))
+    margins = np.zeros(pop.n)
+    ost = np.zeros(pop.n, np.uint32)
+    for i in range(pop.n):
+        m = O.model_from_population(pop32, i)
+        nq, nv, ns = O.nq(m), O.nv(m), 2 * (m.nb - 1)
+        s64 = np.zeros(2 * O.MAXB)
+        s64[:ns] = Sx[i, :ns]
+        q64, v64 = Q[i, :nq].astype(np.float64), V[i, :nv].astype(np.float64)
+        oq, ov, os_, st, stats = O.run(m, q64, v64, s64, 1, prm=prm)
+        vfree = O.step_detail(m, q64, v64, s64, prm=prm)["vfree"]
+        margins[i] = stats.margin
+        ost[i] = st
+        sc = (max(np.linalg.norm(oq[:nq]), 1.0), max(np.linalg.norm(ov[:nv]), np.linalg.norm(vfree), 1.0),
+              max(np.linalg.norm(os_[:ns]), 1.0))
+        for j, (a, b) in enumerate(((gq[i, :nq], oq[:nq]), (gv[i, :nv], ov[:nv]), (gs[i, :ns], os_[:ns]))):
+            errs[i, j] = np.linalg.norm(a - b) / sc[j] if len(b) else 0.0
+    near = margins < 1e-5
+    return errs, near, ost, gst
+
+
+def _check(errs, near, frac_near):
+    bad = (errs.max(axis=1) > TOL) & ~near
+    assert not bad.any(), (errs.max(axis=0), np.nonzero(bad)[0][:10])
+    assert near.mean() <= frac_near
+
+
+def test_one_step_boxes_quadrupeds_grammar():
+    pop = P.boxes(48, seed=1)
+    q = pop.q0.copy()
+    q[:24, 2] = np.random.default_rng(0).uniform(0.03, 0.08, 24)
+    errs, near, ost, gst = _one_step(pop, q, pop.v0, np.zeros((48, 64)))
+    _check(errs, near, 0.1)
+    assert np.array_equal(ost, gst)
+    pop = P.quadrupeds(48, seed=2)
+    q, v, s = P.random_state(pop, seed=5)
+    q[:, 2] = np.random.default_rng(1).uniform(0.03, 0.09, pop.n)
+    _check(*_one_step(pop, q, v, s)[:2], 0.1)
+    pop = P.grammar(96, seed=3)
+    q, v, s = P.random_state(pop, seed=7)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(2).uniform(-0.04, 0.0, pop.n)
+    _check(*_one_step(pop, q, v, s)[:2], 0.25)
+
+
+def test_one_step_largest_robots_and_the_contact_cap():
+    # 26 bodies in random poses: many lattice-aligned bricks sit in exact
+    # separating-axis ties (near-threshold); at least a third are compared
+    pop = P.grammar(36, seed=51, hinges=(25, 25))
+    q, v, s = P.random_state(pop, seed=52)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(53).uniform(-0.03, 0.0, pop.n)
+    _check(*_one_step(pop, q, v, s)[:2], 0.67)
+    pop = P.grammar(48, seed=61)
+    q, v, s = P.random_state(pop, seed=62, angle=0.3)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(63).uniform(-0.045, -0.005, pop.n)
+    errs, near, ost, gst = _one_step(pop, q, v, s, contact_cap=6)
+    _check(errs, near, 0.3)
+    assert ((gst & S.ST_OVERFLOW) != 0).sum() >= 10
+    assert np.array_equal((gst & S.ST_OVERFLOW) != 0, (ost & S.ST_OVERFLOW) != 0)
+
+
+def test_one_step_settled_grammar_states():
+    O = oracle()
+    pop = P.grammar(48, seed=13).as_float32()
+    q, v, s, st, _ = O.run_population(pop, pop.q0, pop.v0, P.cpg_initial(pop), 300,
+                                      threads=len(os.sched_getaffinity(0)))
+    errs, near, _, _ = _one_step(pop, q, v, s)
+    e = errs.max(axis=1)[~near]
+    assert (e <= 2e-5).all() and (e <= TOL).mean() >= 0.95 and np.median(e) <= 1e-6, errs.max(axis=0)
+
+
+def test_contact_free_flight_200_steps():
+    O = oracle()
+    pop = P.lift(P.grammar(32, seed=3), 1.0).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    cs = CP.CpuSim(box_box=0)
+    cs.set_population(pop)
+    cs.set_state(Q, V, Sx)
+    cs.step(200)
+    gq = cs.read_state()[0]
+    oq, _, _, _, _ = O.run_population(pop, Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64),
+                                      200, prm=O.default_params(box_box=0), threads=2)
+    assert np.abs(gq[:, :3] - oq[:, :3]).max() <= 1e-4
+
+
+def test_threads_do_not_change_results_and_frozen_robots_stay_put():
+    pop = P.grammar(40, seed=21).as_float32()
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+    V[7, 9] = np.nan
+    out = []
+    for th in (1, 3):
+        cs = CP.CpuSim(threads=th)
+        cs.set_population(pop)
+        cs.set_state(Q, V, Sx)
+        cs.step(30)
+        out.append(cs.read_state())
+        cs.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b, equal_nan=True)
+    q, v, s, st = out[0]
+    assert st[7] & S.ST_NONFINITE and np.array_equal(q[7], Q[7])
+    assert np.all(st[np.arange(40) != 7] & 5 == 0)
+
+
+def test_abi_errors():
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        CP.CpuSim(pgs_iters=0)
+    cs = CP.CpuSim()
+    with pytest.raises(S.SimError, match="SIM_ESTATE"):
+        cs.step(1)
+    bad = P.quadrupeds(2)
+    bad.parent[1, 3] = 5
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        cs.set_population(bad)
+    cs.set_population(P.quadrupeds(2))
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        cs.read_state(first=1, count=5)
+
+
+def test_hybrid_share_split_and_concurrent_run_on_two_host_engines():
+    assert H.gpu_share(3.0, 1.0) == 0.75 and H.gpu_share(0.0, 2.0) == 0.0
+    with pytest.raises(ValueError):
+        H.gpu_share(0.0, 0.0)
+    g, c = H.split(10, 0.75)
+    assert list(g) == list(range(8)) and list(c) == [8, 9]
+    pop = P.grammar(24, seed=5)
+    r = H.hybrid_point(pop, 20, lambda: CP.CpuSim(threads=2), lambda: CP.CpuSim(threads=1), reps=1)
+    assert r["gpu_variants"] + r["cpu_variants"] == 24
+    assert r["same_as_sequential"]
+    assert abs(r["naive_sum_s"] - (r["seq_gpu_s"] + r["seq_cpu_s"])) < 1e-12

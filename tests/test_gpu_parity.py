@@ -298,3 +298,98 @@ def test_launch_shapes_and_phase_lock_agree_bitwise():
         else:
             for a, b in zip(ref, out):
                 assert np.array_equal(a, b, equal_nan=True), (wpb, lock)
+
+
+def test_one_step_largest_robots_26_bodies():
+    """The maximum model size (25 hinges: 26 bodies, 31 dofs, every lane of
+    the warp a dof) in random poses against the oracle."""
+    pop = P.grammar(48, seed=51, hinges=(25, 25))
+    assert (pop.nb == S.SIM_MAX_BODIES).all()
+    q, v, s = P.random_state(pop, seed=52)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(53).uniform(-0.03, 0.0, pop.n)
+    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
+    near, bad, msg = _report("grammar-26-bodies", errs, margins)
+    assert not bad.any(), msg
+    # lattice-aligned bricks in random poses sit in exact separating-axis
+    # ties (near-threshold); at least a third of the robots are compared
+    assert near.mean() <= 0.67, msg
+
+
+def _contact_counts(sm, n):
+    return np.array([sm.debug_solver(i)["n"] for i in range(n)])
+
+
+def test_one_step_both_sweep_paths_and_the_contact_cap():
+    """Robots pushed into the ground so that steps have more than 10
+    contacts (dof-space sweep) as well as at most 10 (contact-space sweep),
+    then the same states with a cap of 6 (overflow: the 6 deepest kept in
+    list order) -- each against the oracle."""
+    pop = P.grammar(96, seed=61)
+    q, v, s = P.random_state(pop, seed=62, angle=0.3)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(63).uniform(-0.045, -0.005, pop.n)
+    errs, margins, ost, gst, sm = _one_step(pop, q, v, s)
+    nc = _contact_counts(sm, pop.n)
+    assert (nc > 10).sum() >= 10 and (nc <= 10).sum() >= 10, np.bincount(nc)
+    near, bad, msg = _report("both-sweeps", errs, margins)
+    assert not bad.any(), msg
+    errs, margins, ost, gst, sm = _one_step(pop, q, v, s, contact_cap=6)
+    nc = _contact_counts(sm, pop.n)
+    over = (gst & S.ST_OVERFLOW) != 0
+    assert over.sum() >= 20 and (nc <= 6).all()
+    assert np.array_equal(over, (ost & S.ST_OVERFLOW) != 0)
+    near, bad, msg = _report("cap-6", errs, margins)
+    assert not bad.any(), msg
+
+
+def test_empty_and_ragged_inputs():
+    """n = 0 is rejected, a zero-count state transfer is a no-op, and a
+    population whose size is no multiple of any launch shape steps every
+    robot exactly (ragged last block) -- checked against one-robot runs."""
+    sm = S.Sim()
+    empty = P.grammar(3, seed=71).subset(np.zeros(0, np.int64))
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        sm.set_population(empty)
+    pop = P.grammar(37, seed=72).as_float32()
+    sm.set_population(pop)
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    sm.set_state(Q[:0], V[:0], Sx[:0])
+    sm.set_state(Q, V, Sx)
+    sm.step(25)
+    gq = sm.read_state()[0]
+    sm.close()
+    for i in (0, 17, 36):
+        one = _gpu_sim(pop.subset([i]))
+        one.set_state(Q[i:i + 1], V[i:i + 1], Sx[i:i + 1])
+        one.step(25)
+        assert np.array_equal(one.read_state()[0][0], gq[i])
+        one.close()
+
+
+def test_bench_workload_full_size_sampled_one_step():
+    """The timed workload at full size (4096 grammar robots, seed 3) in the
+    bench's launch configuration (autotuned shape, 500-step launches, CUDA
+    graph, slowest-first order): after 1000 steps, one more step of every
+    16th robot from the GPU's FP32 state against the oracle from the same
+    state (the settled-robot bar)."""
+    O = oracle()
+    pop = P.grammar(4096, seed=3).as_float32()
+    s0 = P.cpg_initial(pop)
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
+    sm = _gpu_sim(pop)
+    sm.set_state(Q, V, Sx)
+    sm.autotune(100)
+    sm.set_state(Q, V, Sx)
+    sm.step(1000)
+    Q1, V1, S1, st1 = sm.read_state()
+    sm.close()
+    idx = np.arange(0, 4096, 16)
+    idx = idx[(st1[idx] & 5) == 0]
+    sub = pop.subset(idx)
+    errs, margins, ost, gst, _ = _one_step(sub, Q1[idx].astype(np.float64), V1[idx].astype(np.float64),
+                                           S1[idx].astype(np.float64))
+    near, bad, msg = _report("bench-4096-sampled", errs, margins)
+    e = errs.max(axis=1)[~near]
+    assert (e <= 2e-5).all(), msg
+    assert (e <= TOL_STEP).mean() >= 0.95, msg
+    assert np.median(e) <= 1e-6, msg
