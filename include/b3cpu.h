@@ -62,6 +62,13 @@ int cpu_read_state(cpu_ctx_t* ctx, int32_t first, int32_t count, float* q, float
 /* Core xy displacement of variants [0, n) since their last cpu_set_state. */
 int cpu_fitness(cpu_ctx_t* ctx, float* out, int32_t n);
 
+/* Wall seconds each variant [0, n) (caller's order) took in the last
+ * cpu_step_n (0 for a variant that did not step). */
+int cpu_robot_seconds(cpu_ctx_t* ctx, double* out, int32_t n);
+
+/* Worker threads of cpu_step_n. */
+int cpu_threads(const cpu_ctx_t* ctx);
+
 /* Contacts accumulated over all variants and steps since cpu_set_population. */
 int cpu_contacts(cpu_ctx_t* ctx, double* out);
 

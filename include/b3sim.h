@@ -188,6 +188,12 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
 int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int32_t* n_out,
                      float* cycles_per_step);
 
+/* Cost of each variant [0, n) (caller's order) in the last launch: the SM
+ * clock cycles per step its warp took, sharing its SM with the other warps
+ * (0 before the first launch and for frozen variants).  For schedulers such
+ * as the hybrid CPU + GPU allocation.  Synchronises. */
+int sim_robot_cost(sim_ctx_t* ctx, float* out, int32_t n);
+
 /* Host evaluation of the step kernel's FP64 sine / cosine routine (the one
  * that the hinge angles go through on the device, compiled here for the
  * host): s[i], c[i] for x[i], i < n.  Inspection and testing only; no device

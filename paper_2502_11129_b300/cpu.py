@@ -17,7 +17,7 @@ from . import sim as S
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libb3cpu.so")
 EXPORTS = ["cpu_create", "cpu_destroy", "cpu_set_population", "cpu_set_state", "cpu_step_n", "cpu_read_state",
-           "cpu_fitness", "cpu_contacts", "cpu_last_error"]
+           "cpu_fitness", "cpu_robot_seconds", "cpu_threads", "cpu_contacts", "cpu_last_error"]
 
 _lib = None
 
@@ -38,6 +38,8 @@ def lib():
         L.cpu_read_state.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp]
         L.cpu_fitness.argtypes = [vp, vp, C.c_int32]
         L.cpu_contacts.argtypes = [vp, C.POINTER(C.c_double)]
+        L.cpu_robot_seconds.argtypes = [vp, vp, C.c_int32]
+        L.cpu_threads.argtypes = [vp]
         L.cpu_last_error.argtypes = [vp]
         L.cpu_last_error.restype = C.c_char_p
         _lib = L
@@ -110,6 +112,16 @@ class CpuSim:
         out = np.zeros(n, np.float32)
         self._check(lib().cpu_fitness(self.h, S._ptr(out), n), "cpu_fitness")
         return out
+
+    def robot_seconds(self):
+        """Wall seconds of every robot in the last step call (caller order)."""
+        out = np.zeros(self.n, np.float64)
+        self._check(lib().cpu_robot_seconds(self.h, S._ptr(out), self.n), "cpu_robot_seconds")
+        return out
+
+    @property
+    def threads(self) -> int:
+        return int(lib().cpu_threads(self.h))
 
     def contacts(self) -> float:
         c = C.c_double()

@@ -5,6 +5,7 @@
 // __host__ __device__ helpers it shares with the GPU kernel).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -525,6 +526,7 @@ struct cpu_ctx {
   std::vector<float> q, v, s, fit0;
   std::vector<unsigned> status;
   std::vector<unsigned long long> contacts;  // per robot
+  std::vector<double> seconds;               // per robot, last cpu_step_n
 };
 
 namespace {
@@ -571,6 +573,7 @@ int cpu_set_population(cpu_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
     ctx->fit0.assign((size_t)n * 2, 0.f);
     ctx->status.assign(n, 0u);
     ctx->contacts.assign(n, 0ull);
+    ctx->seconds.assign(n, 0.0);
   } catch (const std::bad_alloc&) {
     ctx->n = 0;
     return fail(ctx, SIM_ENOMEM, "cpu_set_population: out of host memory");
@@ -612,9 +615,11 @@ int cpu_step_n(cpu_ctx_t* ctx, int32_t n_steps) {
                     meta[1], meta[2], meta[3]};
       unsigned st = ctx->status[k];
       unsigned long long nc = 0;
+      const auto t0 = std::chrono::steady_clock::now();
       for (int t = 0; t < n_steps && !(st & 5u); ++t)
         step_robot(m, ctx->pk.pairs.data(), ctx->P, &ctx->q[(size_t)k * 32], &ctx->v[(size_t)k * 32],
                    &ctx->s[(size_t)k * 64], st, nc, *w);
+      ctx->seconds[k] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       ctx->status[k] = st;
       ctx->contacts[k] += nc;
     }
@@ -656,6 +661,16 @@ int cpu_fitness(cpu_ctx_t* ctx, float* out, int32_t n) {
   }
   return SIM_OK;
 }
+
+int cpu_robot_seconds(cpu_ctx_t* ctx, double* out, int32_t n) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "cpu_robot_seconds: no population");
+  if (!out || n < 0 || n > ctx->n) return fail(ctx, SIM_EINVAL, "cpu_robot_seconds: bad n or NULL out");
+  for (int i = 0; i < n; ++i) out[i] = ctx->seconds[ctx->pk.inv[i]];
+  return SIM_OK;
+}
+
+int cpu_threads(const cpu_ctx_t* ctx) { return ctx ? ctx->threads : 0; }
 
 int cpu_contacts(cpu_ctx_t* ctx, double* out) {
   if (!ctx || !out) return SIM_EINVAL;

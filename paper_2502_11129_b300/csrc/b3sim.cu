@@ -361,6 +361,22 @@ cudaError_t noalloc_setup(int dev, NoallocAddrs* out) {
 
 extern "C" {
 
+int sim_robot_cost(sim_ctx_t* ctx, float* out, int32_t n) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_robot_cost: no population");
+  if (!out || n < 0 || n > ctx->n) return fail(ctx, SIM_EINVAL, "sim_robot_cost: bad n or NULL out");
+  if (n == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  std::vector<float> packed(ctx->n);
+  // one float per robot, kScratchFloats apart
+  CK(cudaMemcpy2DAsync(packed.data(), sizeof(float), ctx->d_scratch + b3::kDbgOffset + 31,
+                       b3::kScratchFloats * sizeof(float), sizeof(float), ctx->n, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < n; ++i) out[i] = packed[ctx->inv[i]];
+  return SIM_OK;
+}
+
 int sim_debug_sincos(const double* x, int32_t n, double* s, double* c) {
   if (!x || !s || !c || n < 0) return SIM_EINVAL;
   for (int32_t i = 0; i < n; ++i) b3::sincos_f64(x[i], &s[i], &c[i]);

@@ -164,6 +164,25 @@ def test_hybrid_share_split_and_concurrent_run_on_two_host_engines():
     assert list(g) == list(range(8)) and list(c) == [8, 9]
     pop = P.grammar(24, seed=5)
     r = H.hybrid_point(pop, 20, lambda: CP.CpuSim(threads=2), lambda: CP.CpuSim(threads=1), reps=1)
-    assert r["gpu_variants"] + r["cpu_variants"] == 24
-    assert r["same_as_sequential"]
+    for mode in ("proportional", "longest-first"):
+        assert r[mode]["gpu_variants"] + r[mode]["cpu_variants"] == 24
+        assert r[mode]["same_as_sequential"]
     assert abs(r["naive_sum_s"] - (r["seq_gpu_s"] + r["seq_cpu_s"])) < 1e-12
+
+
+def test_longest_first_split_takes_the_critical_robots():
+    # GPU time set by its heaviest robot (costs 10, 9, then 1s); two CPU
+    # workers step a robot in 0.1 s each.  Taking k robots: CPU ceil(k/2) *
+    # 0.1 s, GPU max(cost of robot k / 10, (8 - k) / 8) s; the best is k = 6
+    # (CPU 0.3 s, GPU max(0.1, 0.25) s)
+    g = np.array([10.0, 9.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0])
+    c = np.full(8, 0.1)
+    gi, ci, t = H.longest_first_split(g, c, t_gpu=1.0, workers=2)
+    assert list(ci) == [0, 1, 2, 3, 4, 5] and list(gi) == [6, 7]
+    assert abs(t - 0.3) < 1e-12
+    # the heaviest robots go first: with one fast worker only two fit
+    gi, ci, t = H.longest_first_split(g, np.array([0.5, 0.5, 1, 1, 1, 1, 1, 1.0]), t_gpu=1.0, workers=1)
+    assert list(ci) == [0] and abs(t - 0.9) < 1e-12
+    # a slow CPU takes nothing
+    gi, ci, t = H.longest_first_split(g, np.full(8, 5.0), t_gpu=1.0, workers=2)
+    assert ci.size == 0 and t == 1.0

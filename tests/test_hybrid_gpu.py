@@ -14,7 +14,9 @@ def test_hybrid_point_runs_both_engines_concurrently():
     pop = P.grammar(512, seed=9)
     r = H.hybrid_point(pop, 100, lambda: S.Sim(), lambda: CP.CpuSim(), reps=1)
     print(r)
-    assert r["gpu_variants"] + r["cpu_variants"] == 512
-    assert r["gpu_variants"] > r["cpu_variants"]  # the B300 is the faster device here
-    assert r["same_as_sequential"]
-    assert r["combined_s"] > 0 and r["seq_cpu_s"] > r["seq_gpu_s"]
+    assert r["seq_cpu_s"] > r["seq_gpu_s"]
+    for mode in ("proportional", "longest-first"):
+        m = r[mode]
+        assert m["gpu_variants"] + m["cpu_variants"] == 512
+        assert m["gpu_variants"] > m["cpu_variants"]  # the B300 is the faster device here
+        assert m["same_as_sequential"] and m["combined_s"] > 0
