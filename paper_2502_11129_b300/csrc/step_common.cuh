@@ -20,6 +20,7 @@ constexpr int kCandW = 8;       // floats per candidate row
 constexpr int kYRows = 3 * kCapMax;
 constexpr float kAmin = 1e-10f;  // rows with J M^-1 J^T at or below this are frozen
 constexpr int kCstW = 12;        // Gauss-Seidel constants per contact (floats)
+constexpr int kMaxPairs = kMaxB * (kMaxB - 1) / 2;  // box/box candidate pairs per robot
 
 // per-variant float model fields, [field][32 body slots]
 enum : int {

@@ -57,6 +57,7 @@ struct __align__(16) WarpSmem {
   int parent[32];
   unsigned path[32];
   unsigned keep[kCand / 32];
+  uint16_t nearp[kMaxPairs];       // near box/box pairs of the step, (a << 8) | b
   unsigned long long ph[kPhases];  // per-phase SM cycles (inspection only)
 };
 
@@ -543,26 +544,37 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     __syncwarp();
     B3_PHASE(3);
     if (P.box_box) {
-      // lane = pair: broad phase, then the narrow phase of every near pair on
-      // its own lane; contacts are placed in pair order by a warp scan
-      float* stage = cand + kStageOffset + (size_t)lane * 8 * kCandW;
+      // broad phase, lane = pair: the near pairs are compacted in pair order
+      // into shared memory, so that the narrow phase below runs once per 32
+      // near pairs rather than once per 32 candidate pairs
+      int nnear = 0;
       for (int p0 = 0; p0 < npairs; p0 += 32) {
         const int pi = p0 + lane;
-        int a = 0, b = 0;
         bool near = false;
+        unsigned pr = 0u;
         if (pi < npairs) {
-          const unsigned pr = pairs[pairoff + pi];
-          a = (int)(pr >> 8);
-          b = (int)(pr & 0xffu);
+          pr = pairs[pairoff + pi];
+          const int a = (int)(pr >> 8), b = (int)(pr & 0xffu);
           const float dx = sm.c[0][b] - sm.c[0][a], dy = sm.c[1][b] - sm.c[1][a], dz = sm.c[2][b] - sm.c[2][a];
           const float rr = __ldg(F + F_RAD * 32 + a) + __ldg(F + F_RAD * 32 + b);
           near = dx * dx + dy * dy + dz * dz <= rr * rr;
         }
-        n_broad += (unsigned)max(0, min(32, npairs - p0));
         const unsigned nm = __ballot_sync(kFull, near);
-        if (!nm) continue;
-        n_narrow += (unsigned)__popc(nm);
-        const int cnt = near ? box_box_lane(sm.R, sm.c, F, a, b, stage) : 0;
+        if (near) sm.nearp[nnear + __popc(nm & ((1u << lane) - 1u))] = (uint16_t)pr;
+        nnear += __popc(nm);
+      }
+      n_broad += (unsigned)npairs;
+      n_narrow += (unsigned)nnear;
+      __syncwarp();
+      // narrow phase, lane = near pair; contacts placed in pair order by a warp scan
+      float* stage = cand + kStageOffset + (size_t)lane * 8 * kCandW;
+      for (int q0 = 0; q0 < nnear; q0 += 32) {
+        const int qi = q0 + lane;
+        int cnt = 0;
+        if (qi < nnear) {
+          const unsigned pr = sm.nearp[qi];
+          cnt = box_box_lane(sm.R, sm.c, F, (int)(pr >> 8), (int)(pr & 0xffu), stage);
+        }
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {

@@ -156,3 +156,44 @@ class Surrogate:
         p = np.ascontiguousarray(flat, np.float32)
         assert p.size == NPARAMS
         self._check(lib().sur_set_params(self.h, _p(p)), "sur_set_params")
+
+
+def timing(n_train=50000, n_screen=65536, k=4096, epochs=3, batch=1024, seed=0) -> dict:
+    """Wall times of the screening workload's surrogate calls (cfg4 sizes) on
+    synthetic genotypes; each call includes its host<->device copies."""
+    import time
+    from . import population as P
+    rng = np.random.default_rng(seed)
+    s = Surrogate(seed=seed)
+    out = {}
+    pop = P.grammar(2048, seed=seed)
+    t = time.perf_counter()
+    X = s.encode(pop)
+    out["encode_2048_s"] = time.perf_counter() - t
+    Xt = rng.normal(0, 0.5, (n_train, IN_DIM)).astype(np.float32)
+    yt = rng.normal(0, 1, n_train).astype(np.float32)
+    s.train(Xt[:batch], yt[:batch], epochs=1, batch=batch)  # warm-up
+    t = time.perf_counter()
+    s.train(Xt, yt, epochs=epochs, batch=batch)
+    dt = time.perf_counter() - t
+    # forward + backward GEMM flops of one sample: 3 x 2 x (128*256 + 256*256 + 256)
+    fl = 6.0 * (IN_DIM * HIDDEN + HIDDEN * HIDDEN + HIDDEN)
+    out.update(train_epochs=epochs, train_s=dt, train_samples_per_s=n_train * epochs / dt,
+               train_tflops_incl_host=fl * n_train * epochs / dt / 1e12)
+    Xs = rng.normal(0, 0.5, (n_screen, IN_DIM)).astype(np.float32)
+    s.predict(Xs[:1024])
+    t = time.perf_counter()
+    y = s.predict(Xs)
+    dt = time.perf_counter() - t
+    out.update(predict_n=n_screen, predict_s=dt, predict_per_s=n_screen / dt,
+               predict_tflops_incl_host=2.0 * (IN_DIM * HIDDEN + HIDDEN * HIDDEN + HIDDEN) * n_screen / dt / 1e12)
+    t = time.perf_counter()
+    s.topk(y, k)
+    out["topk_s"] = time.perf_counter() - t
+    s.close()
+    return out
+
+
+if __name__ == "__main__":
+    import json
+    print(json.dumps(timing()))

@@ -397,3 +397,39 @@ def test_bench_workload_full_size_sampled_one_step():
     assert (e <= TOL_SETTLED_MAX).all(), msg
     assert (e <= TOL_STEP).mean() >= 0.95, msg
     assert np.median(e) <= 1e-6, msg
+
+
+@pytest.mark.parametrize("alpha_deg,slides", [(20.0, False), (35.0, True)])
+def test_incline_stick_slide_on_gpu(alpha_deg, slides):
+    """Tilted gravity on a flat plane = an incline (mu = 0.5, tan a vs mu):
+    free cubes resting on it stick below the friction angle and slide with
+    deceleration g (sin a - mu cos a) above it; the trajectory matches the
+    oracle within 1e-4 m over 500 steps."""
+    O = oracle()
+    G = 9.81
+    a = np.radians(alpha_deg)
+    grav = (G * np.sin(a), 0.0, -G * np.cos(a))
+    pop = P.boxes(16, seed=3).as_float32()
+    q = np.zeros((16, 7))
+    q[:, 2] = 0.0499
+    q[:, 3] = 1.0
+    q[:, 0] = np.arange(16) * 0.3  # the robots are independent anyway
+    v = np.zeros((16, 6))
+    Q, V, Sx = S.state_rows(pop, q, v, np.zeros((16, 64)))
+    sm = _gpu_sim(pop, mu=0.5, gravity=grav)
+    sm.set_state(Q, V, Sx)
+    sm.step(100)
+    v_before = sm.read_state()[1][:, 0].copy()
+    sm.step(400)
+    gq, gv, _, gst = sm.read_state()
+    assert (gst & 5).sum() == 0
+    if slides:
+        acc = (gv[:, 0] - v_before) / (400 * 0.002)
+        assert np.abs(acc - G * (np.sin(a) - 0.5 * np.cos(a))).max() < 0.01 * G * np.sin(a)
+    else:
+        assert np.abs(gv[:, 0]).max() < 0.02
+        assert np.abs(gq[:, 0] - q[:, 0]).max() < 0.02
+    prm = O.default_params(mu=0.5, gravity=grav)
+    oq, _, _, _, _ = O.run_population(pop, Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64), 500,
+                                      prm=prm, threads=ncores())
+    assert np.abs(gq[:, :3] - oq[:, :3]).max() <= 1e-4
