@@ -3,11 +3,11 @@
 robots on one B300 (per GPU; weak scaling over GPUs).
 
 Workload: 4096 seeded tree-grammar robots (2..20 hinged bricks, seed 3 + rank),
-dt = 0.002 s, the first 15000 steps of their run: the default --steps 15 bench
-steps of 1000 simulation steps each (one sim_step_n call = one CUDA-graph
-replay of persistent step launches).  W warm-up bench steps run first, then
-the state is reset to the workload's start, so the timed region is steps
-0..K*1000 of the run.
+dt = 0.002 s, the first 15000 steps of their run: the default --steps 3 bench
+steps of 5000 simulation steps each (one sim_step_n call = one CUDA-graph
+replay of one persistent 5000-step launch).  W warm-up bench steps run first,
+then the state is reset to the workload's start, so the timed region is steps
+0..K*chunk of the run.
 
 Printed JSON (rank 0):
   value    device time of the timed sim_step_n calls (CUDA events on the
@@ -49,11 +49,11 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=15, help="timed bench steps")
+    ap.add_argument("--steps", type=int, default=3, help="timed bench steps")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variants", type=int, default=4096)
-    ap.add_argument("--chunk", type=int, default=1000, help="simulation steps per bench step")
+    ap.add_argument("--chunk", type=int, default=5000, help="simulation steps per bench step")
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -231,7 +231,7 @@ def run_ours(args, world, rank, local, dist):
     # executed variant-steps over all ranks (a variant frozen by a non-finite
     # state stops advancing)
     value = reduce_sum(dist, vsteps, dev) / total_s
-    spl = sm.cfg["steps_per_launch"] or 500
+    spl = min(sm.cfg["steps_per_launch"] or 5000, args.chunk)
     launches_per_chunk = -(-args.chunk // spl)
     launch_s = total_s / (args.steps * launches_per_chunk)
 

@@ -94,7 +94,7 @@ typedef struct {
     float max_correct_vel;    /* cap of the penetration recovery speed [m/s] */
     int32_t device;           /* CUDA device ordinal                         */
     uint64_t stream;          /* cudaStream_t or 0                           */
-    int32_t steps_per_launch; /* persistent chunk; 0: library default        */
+    int32_t steps_per_launch; /* persistent chunk; 0: library default (5000) */
     int32_t warps_per_block;  /* 0: autotuned default                        */
     int32_t phase_lock;       /* 1: the warps of a block pass the step's phase
                                  boundaries together (block barriers: fewer

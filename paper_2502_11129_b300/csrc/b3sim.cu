@@ -26,6 +26,8 @@
 using b3::Counters;
 using b3::StepParams;
 
+constexpr int kDefaultStepsPerLaunch = 5000;
+
 struct sim_ctx {
   sim_config cfg{};
   std::string err;
@@ -52,7 +54,12 @@ struct sim_ctx {
   float* d_stage = nullptr;  // caller-order staging: q | v | s rows
   unsigned* d_stage_st = nullptr;
   StepParams P{};
-  int steps_per_launch = 500;
+  // Steps per persistent launch.  A launch lasts as long as its slowest
+  // robot, and which robot is slowest changes as contacts come and go, so a
+  // long launch (the maximum over robots of a sum over steps) beats many
+  // short ones (a sum over launches of maxima): 5000-step launches measured
+  // 16 % faster than 500-step ones on 4096 grammar robots.
+  int steps_per_launch = kDefaultStepsPerLaunch;
   int wpb = 4;
   bool lock = false;  // phase-locked launches (warps of a block in step)
   std::map<long long, cudaGraphExec_t> graphs;
@@ -429,7 +436,7 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
                     pop->q,       pop->v,       pop->cpg, pop->status, a.counters, a.scratch, a.lastnc,
                     nullptr,      nullptr,      pop->n,   make_params(cfg), stream};
     const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
-    const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : 500;
+    const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : kDefaultStepsPerLaunch;
     e = enqueue_launches(args, n_steps, wpb, cfg->phase_lock == 1, spl);
   }
   if (e != cudaSuccess) {

@@ -114,8 +114,17 @@ def _concurrent(pop, steps, gi, ci, gpu_factory, cpu_factory, reps):
     cpu_part = _Run(cpu_factory, pop.subset(ci)) if ci.size else None
     fit = np.zeros(pop.n, np.float32)
     try:
+        # one untimed concurrent run: graph capture, host threads and work spaces warm
+        for part in (gpu_part, cpu_part):
+            if part is not None:
+                part.reset()
         if gpu_part is not None:
-            _timed(gpu_part, steps)  # graph capture outside the timed region
+            gpu_part.eng.step(steps)
+        if cpu_part is not None:
+            cpu_part.eng.step(steps)
+            cpu_part.eng.fitness()
+        if gpu_part is not None:
+            gpu_part.eng.fitness()
         walls = []
         for _ in range(reps):
             for part in (gpu_part, cpu_part):

@@ -324,16 +324,17 @@ def _contact_counts(sm, n):
 
 
 def test_one_step_both_sweep_paths_and_the_contact_cap():
-    """Robots pushed into the ground so that steps have more than 10
-    contacts (dof-space sweep) as well as at most 10 (contact-space sweep),
-    then the same states with a cap of 6 (overflow: the 6 deepest kept in
-    list order) -- each against the oracle."""
-    pop = P.grammar(96, seed=61)
+    """Robots pushed into the ground so that steps have at most 10 contacts
+    (contact-space sweep) as well as more (dof-space sweep), then the same
+    states with a cap of 6 (overflow: the 6 deepest kept in list order) --
+    each against the oracle."""
+    pop = P.grammar(128, seed=61)
     q, v, s = P.random_state(pop, seed=62, angle=0.3)
-    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(63).uniform(-0.045, -0.005, pop.n)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(63).uniform(-0.06, -0.005, pop.n)
     errs, margins, ost, gst, sm = _one_step(pop, q, v, s)
     nc = _contact_counts(sm, pop.n)
-    assert (nc > 10).sum() >= 10 and (nc <= 10).sum() >= 10, np.bincount(nc)
+    print("contact counts", np.bincount(nc))
+    assert (nc <= 10).sum() >= 10 and (nc > 10).sum() >= 10, np.bincount(nc)
     near, bad, msg = _report("both-sweeps", errs, margins)
     assert not bad.any(), msg
     errs, margins, ost, gst, sm = _one_step(pop, q, v, s, contact_cap=6)
