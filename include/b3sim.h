@@ -166,6 +166,12 @@ int sim_fitness(sim_ctx_t* ctx, float* out, int32_t n);
  * population (state is saved and restored) and keep the fastest. */
 int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps);
 
+/* The launch shape sim_step_n uses now (after sim_autotune, the chosen one):
+ * warps per block, phase lock and steps per persistent launch.  Any output
+ * may be NULL. */
+int sim_launch_shape(const sim_ctx_t* ctx, int32_t* warps_per_block, int32_t* phase_lock,
+                     int32_t* steps_per_launch);
+
 /* Work counters accumulated since sim_set_population (synchronises). */
 int sim_counters_read(sim_ctx_t* ctx, sim_counters* out);
 

@@ -229,7 +229,43 @@ __global__ void cost_init(const int4* __restrict__ meta, int n, float* __restric
   scratch[(size_t)i * b3::kScratchFloats + b3::kDbgOffset + 31] = 1000.f * nb * nb;
 }
 
+// Up to kSortMax robots the order is deterministic: one block sorts the keys
+// (bucket << 24 | robot) with a bitonic network in shared memory, so robots
+// of equal cost keep their packed order and every run launches robots in the
+// same order.  Larger populations use the atomic bucket scatter above (the
+// order inside a bucket then varies from run to run; only timing depends on it).
+constexpr int kSortMax = 8192;  // 32 KB of static shared memory
+
+__global__ void __launch_bounds__(1024) cost_sort(const float* __restrict__ scratch, int n, int* __restrict__ order) {
+  __shared__ unsigned key[kSortMax];
+  int m = 1;
+  while (m < n) m <<= 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    key[i] = i < n ? ((unsigned)cost_bucket(scratch[(size_t)i * b3::kScratchFloats + b3::kDbgOffset + 31]) << 24) |
+                         (unsigned)i
+                   : 0xffffffffu;
+  __syncthreads();
+  for (int size = 2; size <= m; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const unsigned a = key[i], b = key[j];
+          if ((a > b) == up) { key[i] = b; key[j] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int)(key[i] & 0xffffffu);
+}
+
 cudaError_t cost_order(const LaunchArgs& a) {
+  if (a.n <= kSortMax) {
+    cost_sort<<<1, 1024, 0, a.stream>>>(a.scratch, a.n, a.order);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(a.order_hist, 0, 2 * kCostBuckets * sizeof(unsigned), a.stream);
   if (e != cudaSuccess) return e;
   const int nb = (a.n + 255) / 256;
@@ -708,6 +744,15 @@ int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
   cudaEventDestroy(e1);
   CK(restore());
   ctx->wpb = best;
+  return SIM_OK;
+}
+
+int sim_launch_shape(const sim_ctx_t* ctx, int32_t* warps_per_block, int32_t* phase_lock,
+                     int32_t* steps_per_launch) {
+  if (!ctx) return SIM_EINVAL;
+  if (warps_per_block) *warps_per_block = ctx->wpb;
+  if (phase_lock) *phase_lock = ctx->lock ? 1 : 0;
+  if (steps_per_launch) *steps_per_launch = ctx->steps_per_launch;
   return SIM_OK;
 }
 

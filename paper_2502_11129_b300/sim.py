@@ -25,7 +25,7 @@ STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: 
 
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
            "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
-           "sim_debug_contacts", "sim_debug_solver", "sim_debug_sincos", "sim_robot_cost", "sim_step_n_noalloc", "sim_last_error"]
+           "sim_debug_contacts", "sim_debug_solver", "sim_debug_sincos", "sim_robot_cost", "sim_launch_shape", "sim_step_n_noalloc", "sim_last_error"]
 
 
 class SimConfig(C.Structure):
@@ -97,6 +97,7 @@ def lib():
         L.sim_step_n_noalloc.argtypes = [P(SimConfig), P(DevicePopulation), C.c_int32]
         L.sim_debug_sincos.argtypes = [vp, C.c_int32, vp, vp]
         L.sim_robot_cost.argtypes = [vp, vp, C.c_int32]
+        L.sim_launch_shape.argtypes = [vp, vp, vp, vp]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
@@ -256,6 +257,12 @@ class Sim:
         m = min(n.value, max_contacts)
         return dict(n=n.value, p=rows[:m, 0:3], nrm=rows[:m, 3:6], depth=rows[:m, 6],
                     a=rows[:m, 7].astype(np.int32), b=bb[:m])
+
+    def launch_shape(self) -> dict:
+        """Launch shape in use (warps per block, phase lock, steps per launch)."""
+        w, lk, spl = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(lib().sim_launch_shape(self.h, C.byref(w), C.byref(lk), C.byref(spl)), "sim_launch_shape")
+        return dict(warps_per_block=w.value, phase_lock=lk.value, steps_per_launch=spl.value)
 
     def robot_cost(self):
         """SM cycles per step of every robot in the last launch (caller order)."""
