@@ -152,7 +152,7 @@ class Clocks:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step_kernel.cuh", "step_common.cuh", "b3sim.cu"):
+    for f in ("step_kernel.cuh", "step_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2502_11129_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
