@@ -96,6 +96,9 @@ typedef struct {
     uint64_t stream;          /* cudaStream_t or 0                           */
     int32_t steps_per_launch; /* persistent chunk; 0: library default (5000) */
     int32_t warps_per_block;  /* 0: autotuned default                        */
+    float min_cfm;            /* floor of a contact row's softness R [1/kg]:
+                                 R = max(kappa A, min_cfm); bounds the
+                                 impulse of rows the dofs can barely move    */
     int32_t phase_lock;       /* 1: the warps of a block pass the step's phase
                                  boundaries together (block barriers: fewer
                                  distinct phases per SM at a time, but every

@@ -68,7 +68,7 @@ class Params(C.Structure):
         ("kp", C.c_double), ("kd", C.c_double), ("tau_max", C.c_double),
         ("theta_max", C.c_double), ("armature", C.c_double),
         ("ground", C.c_int32), ("box_box", C.c_int32), ("actuate", C.c_int32),
-        ("max_correct_vel", C.c_double),
+        ("max_correct_vel", C.c_double), ("min_cfm", C.c_double),
     ]
 
 

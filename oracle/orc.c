@@ -138,6 +138,7 @@ void orc_default_params(orc_params* p) {
     p->box_box = 1;
     p->actuate = 1;
     p->max_correct_vel = 0.1;
+    p->min_cfm = 0.1;
 }
 
 static void setup(work* w, const orc_model* m) {
@@ -841,7 +842,12 @@ static int step(work* w, const orc_model* m, const orc_params* prm, double* q, d
                plane of a planar mechanism) carries no impulse: frozen at 0 */
             note_margin(w, (a - ORC_AMIN) * 1e4);
             w->A[r] = a > ORC_AMIN ? a : 0.0;
-            w->Rs[r] = kappa * a;
+            /* softness R = kappa A (mass-normalised CFM), floored: a row that the
+               dofs can barely move (A -> 0 but above the freeze threshold) would
+               otherwise take an impulse ~ 1 / A and inject ~ g^2 / (2 A) of
+               kinetic energy; with R >= min_cfm a row's kinetic energy change
+               is at most g^2 / (8 min_cfm) */
+            w->Rs[r] = kappa * a > prm->min_cfm ? kappa * a : prm->min_cfm;
             if (d == 0) {
                 /* penetration recovery speed, capped (ODE's maximum correcting velocity) */
                 double tn = erp * w->con.depth[k] / dt;

@@ -69,6 +69,7 @@ typedef struct {
     int32_t box_box;            /* box/box contacts on                      */
     int32_t actuate;            /* CPG + PD torques on                      */
     double max_correct_vel;     /* cap of the penetration recovery speed    */
+    double min_cfm;             /* floor of a row's softness R [1/kg]       */
 } orc_params;
 
 typedef struct {

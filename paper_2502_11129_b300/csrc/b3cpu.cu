@@ -386,7 +386,7 @@ bool step_robot(const Robot& m, const uint16_t* pairs, const StepParams& P, floa
       yr[i] = yi;
       aa += yi * yi;
     }
-    const float Rr = P.kappa * aa;
+    const float Rr = std::fmax(P.kappa * aa, P.min_cfm);  // floored softness (see the GPU kernel)
     const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
     const float bias = dir == 0 ? jv - std::fmin(P.erp * depth_k / dt, P.max_correct_vel) : jv;
     w.cst[k][3 * dir] = bias;
@@ -511,6 +511,7 @@ StepParams params_of(const sim_config* cfg) {
   P.box_box = cfg->box_box ? 1 : 0;
   P.actuate = cfg->actuate ? 1 : 0;
   P.max_correct_vel = cfg->max_correct_vel;
+  P.min_cfm = cfg->min_cfm;
   return P;
 }
 
@@ -543,7 +544,7 @@ int cpu_create(const sim_config* cfg, int32_t threads, cpu_ctx_t** out) {
   *out = nullptr;
   if (!cfg || threads < 0 || !(cfg->dt > 0.0) || cfg->pgs_iters < 1 || cfg->contact_cap < 1 ||
       cfg->contact_cap > SIM_MAX_CONTACT_CAP || !(cfg->soft_tau > 0.f) || !(cfg->soft_zeta >= 0.f) ||
-      !(cfg->mu >= 0.f) || !(cfg->max_correct_vel > 0.f))
+      !(cfg->mu >= 0.f) || !(cfg->max_correct_vel > 0.f) || !(cfg->min_cfm >= 0.f))
     return SIM_EINVAL;
   cpu_ctx* ctx = new (std::nothrow) cpu_ctx;
   if (!ctx) return SIM_ENOMEM;

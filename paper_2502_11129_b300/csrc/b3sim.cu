@@ -327,7 +327,7 @@ cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int spl
 bool config_ok(const sim_config* cfg) {
   return cfg->dt > 0.0 && cfg->pgs_iters >= 1 && cfg->contact_cap >= 1 &&
          cfg->contact_cap <= SIM_MAX_CONTACT_CAP && cfg->soft_tau > 0.f && cfg->soft_zeta >= 0.f &&
-         cfg->mu >= 0.f && cfg->steps_per_launch >= 0 && cfg->max_correct_vel > 0.f &&
+         cfg->mu >= 0.f && cfg->steps_per_launch >= 0 && cfg->max_correct_vel > 0.f && cfg->min_cfm >= 0.f &&
          (cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
           cfg->warps_per_block == 4 || cfg->warps_per_block == 8) &&
          (cfg->phase_lock == 0 || cfg->phase_lock == 1);
@@ -358,6 +358,7 @@ StepParams make_params(const sim_config* cfg) {
   P.box_box = cfg->box_box ? 1 : 0;
   P.actuate = cfg->actuate ? 1 : 0;
   P.max_correct_vel = cfg->max_correct_vel;
+  P.min_cfm = cfg->min_cfm;
   return P;
 }
 

@@ -46,6 +46,7 @@ struct StepParams {
   float kp, kd, tau_max, theta_max, armature;
   int ground, box_box, actuate;
   float max_correct_vel;
+  float min_cfm;
 };
 
 __host__ __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }

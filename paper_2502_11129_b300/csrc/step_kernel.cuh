@@ -710,7 +710,9 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 #pragma unroll 1
         for (int i = 0; i < 8; ++i)
           dst[i] = make_float4(yr[32 * (4 * i)], yr[32 * (4 * i + 1)], yr[32 * (4 * i + 2)], yr[32 * (4 * i + 3)]);
-        const float Rr = P.kappa * aa;
+        // softness kappa A (mass-normalised CFM), floored at min_cfm: a row the
+        // dofs can barely move would otherwise take an impulse ~ 1/A
+        const float Rr = fmaxf(P.kappa * aa, P.min_cfm);
         // a row that no dof can move (J = 0) carries no impulse: 1/(A+R) = 0
         const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
         // penetration recovery speed, capped (ODE's maximum correcting velocity)

@@ -36,7 +36,7 @@ class SimConfig(C.Structure):
         ("tau_max", C.c_float), ("theta_max", C.c_float), ("armature", C.c_float),
         ("ground", C.c_int32), ("box_box", C.c_int32), ("actuate", C.c_int32),
         ("max_correct_vel", C.c_float), ("device", C.c_int32), ("stream", C.c_uint64), ("steps_per_launch", C.c_int32),
-        ("warps_per_block", C.c_int32), ("phase_lock", C.c_int32),
+        ("warps_per_block", C.c_int32), ("min_cfm", C.c_float), ("phase_lock", C.c_int32),
     ]
 
 
@@ -65,7 +65,7 @@ class Counters(C.Structure):
 DEFAULTS = dict(dt=0.002, gravity=(0.0, 0.0, -9.81), pgs_iters=30, soft_tau=0.02, soft_zeta=1.0,
                 mu=1.0, contact_cap=64, kp=2.0, kd=0.05, tau_max=1.0, theta_max=np.pi / 2,
                 armature=1e-4, ground=1, box_box=1, actuate=1, max_correct_vel=0.1, device=0, stream=0,
-                steps_per_launch=0, warps_per_block=0, phase_lock=0)
+                steps_per_launch=0, warps_per_block=0, min_cfm=0.1, phase_lock=0)
 
 _lib = None
 

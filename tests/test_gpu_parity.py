@@ -434,3 +434,25 @@ def test_incline_stick_slide_on_gpu(alpha_deg, slides):
     oq, _, _, _, _ = O.run_population(pop, Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64), 500,
                                       prm=prm, threads=ncores())
     assert np.abs(gq[:, :3] - oq[:, :3]).max() <= 1e-4
+
+
+def test_heavy_cubes_rest_on_the_softness_floor_on_gpu():
+    """100 kg cubes (kappa A below min_cfm): the GPU's steady depth equals the
+    closed form min_cfm lambda dt / ERP within 1e-6 m."""
+    pop = P.boxes(8, seed=5).as_float32()
+    pop.mass[:, 0] = 100.0
+    q = np.zeros((8, 7))
+    q[:, 2] = 0.0501
+    q[:, 3] = 1.0
+    Q, V, Sx = S.state_rows(pop, q, np.zeros((8, 6)), np.zeros((8, 64)))
+    sm = _gpu_sim(pop)
+    sm.set_state(Q, V, Sx)
+    sm.step(4000)
+    gq, gv, _, gst = sm.read_state()
+    dt, G = 0.002, 9.81
+    omg = 2 * np.pi / 0.02
+    kden = dt * omg * omg + 2 * omg
+    erp = dt * omg * omg / kden
+    dstar = 0.1 * (100.0 * G * dt / 4) * dt / erp
+    assert (gst & 5).sum() == 0
+    assert np.abs(gq[:, 2] - (0.05 - dstar)).max() < 1e-6

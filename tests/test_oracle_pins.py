@@ -595,6 +595,32 @@ def test_resting_cube_steady_penetration():
     assert np.abs(v).max() < 1e-6
 
 
+def test_heavy_cube_rests_on_the_softness_floor():
+    """100 kg cube of the same size: kappa A = kappa * 4 / 100 < min_cfm, so
+    the floored softness R = min_cfm sets the steady depth d* = min_cfm
+    lambda dt / ERP (lambda = m g dt / 4 per corner), four times the depth
+    kappa A would give; the recovery speed ERP d* / dt stays below the cap."""
+    m = H.single_box(mass=100.0)
+    p = O.default_params()
+    q = free_q((0.0, 0.0, 0.0501))
+    v = np.zeros(6)
+    q, v, _, st, _ = O.run(m, q, v, np.zeros(2), 4000, prm=p)
+    omg = 2 * np.pi / p.soft_tau
+    kden = p.dt * omg * omg + 2 * p.soft_zeta * omg
+    erp = p.dt * omg * omg / kden
+    kappa = 1.0 / (p.dt * kden)
+    I = 100.0 * 0.1 ** 2 / 6
+    A = 1.0 / 100.0 + (0.05 ** 2 + 0.05 ** 2) / I
+    assert kappa * A < p.min_cfm
+    lam = 100.0 * G * p.dt / 4
+    dstar = p.min_cfm * lam * p.dt / erp
+    assert erp * dstar / p.dt < p.max_correct_vel
+    assert st == 0
+    assert abs(q[2] - (0.05 - dstar)) < 1e-6
+    assert abs(dstar - kappa * A * lam * p.dt / erp) > 1e-4  # the floor, not kappa A, decides
+    assert np.abs(v).max() < 1e-6
+
+
 @pytest.mark.parametrize("alpha_deg,slides", [(20.0, False), (35.0, True)])
 def test_incline_stick_slide(alpha_deg, slides):
     """Tilted gravity on a flat plane = an incline: with mu = 0.5 the cube
