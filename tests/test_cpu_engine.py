@@ -35,7 +35,8 @@ def _one_step(pop, q, v, s, **cfg):
     cs.step(1)
     gq, gv, gs, gst = cs.read_state()
     cs.close()
-    keep = {k: val for k, val in cfg.items() if k in ("contact_cap", "box_box", "ground", "actuate")}
+    keep = {k: val for k, val in cfg.items() if k in ("contact_cap", "box_box", "ground", "actuate",
+                                                       "max_correct_vel", "min_cfm")}
     prm = O.default_params(**keep)
     errs = np.zeros((pop.n, 3))
     margins = np.zeros(pop.n)

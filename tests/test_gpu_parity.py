@@ -52,7 +52,8 @@ def _gpu_sim(pop, **cfg):
 
 def _oracle_params(O, **cfg):
     keep = {k: v for k, v in cfg.items() if k in ("dt", "gravity", "pgs_iters", "mu", "contact_cap",
-                                                 "ground", "box_box", "actuate", "armature")}
+                                                 "ground", "box_box", "actuate", "armature",
+                                                 "max_correct_vel", "min_cfm")}
     return O.default_params(**keep)
 
 
