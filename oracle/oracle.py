@@ -57,6 +57,7 @@ class Model(C.Structure):
         ("mass", C.c_double * MAXB), ("w_int", C.c_double * MAXB),
         ("w_cpl", C.c_double * MAXB),
         ("root_R", C.c_double * 9), ("root_p", C.c_double * 3),
+        ("geom", C.c_int32 * MAXB),
     ]
 
 
@@ -162,6 +163,7 @@ def model_from_population(pop, i: int) -> Model:
         m.mass[b] = float(pop.mass[i, b])
         m.w_int[b] = float(pop.w_int[i, b])
         m.w_cpl[b] = float(pop.w_cpl[i, b])
+        m.geom[b] = int(pop.geom[i, b])
     for k in range(9):
         m.root_R[k] = 1.0 if k in (0, 4, 8) else 0.0
     return m

@@ -195,10 +195,18 @@ static void body_inertias(work* w, const orc_model* m) {
     for (int b = 0; b < m->nb; ++b) {
         const double* h = m->half[b];
         double mb = m->mass[b];
-        double Id[3] = {mb * (h[1] * h[1] + h[2] * h[2]) / 3.0,
-                        mb * (h[0] * h[0] + h[2] * h[2]) / 3.0,
-                        mb * (h[0] * h[0] + h[1] * h[1]) / 3.0};
-        FL(w, 18);
+        /* principal moments about the centre: solid box m (h_j^2 + h_k^2) / 3,
+         * solid sphere 2 m r^2 / 5 */
+        double Id[3];
+        if (m->geom[b] == ORC_GEOM_SPHERE) {
+            Id[0] = Id[1] = Id[2] = 0.4 * mb * h[0] * h[0];
+            FL(w, 3);
+        } else {
+            Id[0] = mb * (h[1] * h[1] + h[2] * h[2]) / 3.0;
+            Id[1] = mb * (h[0] * h[0] + h[2] * h[2]) / 3.0;
+            Id[2] = mb * (h[0] * h[0] + h[1] * h[1]) / 3.0;
+            FL(w, 18);
+        }
         const double* R = w->R[b];
         double Iw[9];
         for (int i = 0; i < 3; ++i)
@@ -438,6 +446,15 @@ static void cand_add(orc_contact_list* cl, int a, int b, const double* p, const 
 static void plane_contacts(work* w, const orc_model* m) {
     static const double up[3] = {0.0, 0.0, 1.0};
     for (int b = (m->root_fixed ? 1 : 0); b < m->nb; ++b) {
+        if (m->geom[b] == ORC_GEOM_SPHERE) {
+            /* sphere/plane: the lowest point of the sphere, if below z = 0 */
+            double r = m->half[b][0];
+            double pw[3] = {w->O[0] + w->c[b][0], w->O[1] + w->c[b][1], w->O[2] + w->c[b][2] - r};
+            FL(w, 4);
+            note_margin(w, pw[2]);
+            if (pw[2] < 0.0) cand_add(&w->cand, b, -1, pw, up, -pw[2]);
+            continue;
+        }
         for (int k = 0; k < 8; ++k) {
             double lv[3], t[3], pw[3];
             for (int i = 0; i < 3; ++i) lv[i] = m->com[b][i] + (((k >> i) & 1) ? 1.0 : -1.0) * m->half[b][i];
@@ -634,6 +651,83 @@ static void box_box(work* w, const orc_model* m, int ia, int ib) {
     }
 }
 
+/* Sphere/sphere and sphere/box, one contact at most.  The point is midway
+ * between the two surfaces' deepest points along the normal; normals point
+ * from body ib (higher index) towards body ia.
+ *   sphere/sphere: n along the centre difference, depth r_a + r_b - |d|;
+ *   sphere/box: Q = the box point closest to the sphere centre C (C clamped
+ *     to the box in box axes); C outside: n = (C - Q) / |C - Q|, depth
+ *     r - |C - Q|; C inside: n = the normal of the nearest face (smallest
+ *     h_k - |C_k|, ties to the lowest k), depth r + h_k - |C_k|. */
+static void sphere_pair(work* w, const orc_model* m, int ia, int ib) {
+    w->narrow++;
+    int sa = m->geom[ia] == ORC_GEOM_SPHERE, sb = m->geom[ib] == ORC_GEOM_SPHERE;
+    double p[3], n[3];
+    if (sa && sb) {
+        double ra = m->half[ia][0], rb = m->half[ib][0];
+        double d[3] = {w->c[ia][0] - w->c[ib][0], w->c[ia][1] - w->c[ib][1], w->c[ia][2] - w->c[ib][2]};
+        double dist = sqrt(dot3(w, d, d));
+        double depth = ra + rb - dist;
+        FL(w, 3 + 1 + 2);
+        note_margin(w, depth);
+        if (!(depth > 0.0) || !(dist > 0.0)) return;
+        for (int k = 0; k < 3; ++k) {
+            n[k] = d[k] / dist;
+            p[k] = w->O[k] + 0.5 * ((w->c[ia][k] - ra * n[k]) + (w->c[ib][k] + rb * n[k]));
+        }
+        FL(w, 3 * 8);
+        cand_add(&w->cand, ia, ib, p, n, depth);
+        return;
+    }
+    int is = sa ? ia : ib, ix = sa ? ib : ia;  /* the sphere and the box */
+    double r = m->half[is][0];
+    const double* h = m->half[ix];
+    const double* R = w->R[ix];
+    double D[3] = {w->c[is][0] - w->c[ix][0], w->c[is][1] - w->c[ix][1], w->c[is][2] - w->c[ix][2]};
+    double l[3], q[3], e[3];
+    for (int k = 0; k < 3; ++k) {
+        l[k] = R[k] * D[0] + R[3 + k] * D[1] + R[6 + k] * D[2];  /* R^T D: box axes */
+        q[k] = l[k] > h[k] ? h[k] : (l[k] < -h[k] ? -h[k] : l[k]);
+        e[k] = l[k] - q[k];
+    }
+    FL(w, 3 + 3 * 5 + 3);
+    double e2 = dot3(w, e, e);
+    double nl[3], pl[3], depth;
+    if (e2 > 0.0) {
+        double dist = sqrt(e2);
+        depth = r - dist;
+        FL(w, 2);
+        note_margin(w, depth);
+        note_margin(w, dist);
+        if (!(depth > 0.0)) return;
+        for (int k = 0; k < 3; ++k) { nl[k] = e[k] / dist; pl[k] = q[k] - 0.5 * depth * nl[k]; }
+        FL(w, 3 * 4);
+    } else {
+        int kk = 0;
+        double pen = h[0] - fabs(l[0]);
+        for (int k = 1; k < 3; ++k) {
+            double pk = h[k] - fabs(l[k]);
+            if (pk < pen) { pen = pk; kk = k; }
+        }
+        FL(w, 3 * 2);
+        for (int k = 0; k < 3; ++k) if (k != kk) note_margin(w, (h[k] - fabs(l[k])) - pen);
+        note_margin(w, h[kk] - pen);  /* distance of the centre from the surface */
+        depth = r + pen;
+        for (int k = 0; k < 3; ++k) nl[k] = 0.0;
+        nl[kk] = l[kk] >= 0.0 ? 1.0 : -1.0;
+        for (int k = 0; k < 3; ++k) pl[k] = l[k] + 0.5 * (pen - r) * nl[k];
+        FL(w, 1 + 3 * 4);
+    }
+    /* to world; the box-to-sphere normal is flipped when the sphere is ib */
+    double sg = is == ia ? 1.0 : -1.0;
+    for (int k = 0; k < 3; ++k) {
+        n[k] = sg * (R[3 * k] * nl[0] + R[3 * k + 1] * nl[1] + R[3 * k + 2] * nl[2]);
+        p[k] = w->O[k] + w->c[ix][k] + (R[3 * k] * pl[0] + R[3 * k + 1] * pl[1] + R[3 * k + 2] * pl[2]);
+    }
+    FL(w, 3 * 6 + 3 * 7);
+    cand_add(&w->cand, ia, ib, p, n, depth);
+}
+
 static int gen_contacts(work* w, const orc_model* m, const orc_params* prm) {
     w->phase = ORC_PH_CONTACT;
     w->cand.n = 0;
@@ -641,9 +735,13 @@ static int gen_contacts(work* w, const orc_model* m, const orc_params* prm) {
     if (prm->box_box) {
         double rad[ORC_MAXB];
         for (int b = 0; b < m->nb; ++b) {
-            rad[b] = sqrt(m->half[b][0] * m->half[b][0] + m->half[b][1] * m->half[b][1] +
-                          m->half[b][2] * m->half[b][2]);
-            FL(w, 6);
+            if (m->geom[b] == ORC_GEOM_SPHERE) {
+                rad[b] = m->half[b][0];
+            } else {
+                rad[b] = sqrt(m->half[b][0] * m->half[b][0] + m->half[b][1] * m->half[b][1] +
+                              m->half[b][2] * m->half[b][2]);
+                FL(w, 6);
+            }
         }
         for (int a = 0; a < m->nb; ++a)
             for (int b = a + 1; b < m->nb; ++b) {
@@ -652,7 +750,10 @@ static int gen_contacts(work* w, const orc_model* m, const orc_params* prm) {
                 double d[3] = {w->c[b][0] - w->c[a][0], w->c[b][1] - w->c[a][1], w->c[b][2] - w->c[a][2]};
                 double rr = rad[a] + rad[b];
                 FL(w, 4 + 5 + 2);
-                if (dot3(w, d, d) <= rr * rr) box_box(w, m, a, b);
+                if (dot3(w, d, d) <= rr * rr) {
+                    if (m->geom[a] == ORC_GEOM_BOX && m->geom[b] == ORC_GEOM_BOX) box_box(w, m, a, b);
+                    else sphere_pair(w, m, a, b);
+                }
             }
     }
     /* keep the contact_cap deepest, ties by list order, list order kept */

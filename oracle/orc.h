@@ -17,7 +17,8 @@
  *     (Featherstone 2008, ch. 6), plus a hinge armature;
  *   - dense Cholesky M = L L^T, unconstrained velocity v + dt M^-1 (tau - c);
  *   - contacts: box/plane vertices, box/box by the separating-axis test with
- *     face clipping (Sutherland-Hodgman) or an edge-edge point;
+ *     face clipping (Sutherland-Hodgman) or an edge-edge point; sphere/plane,
+ *     sphere/box (closest point of the box) and sphere/sphere, one point each;
  *   - soft projected Gauss-Seidel on contact impulses (ODE ERP/CFM soft
  *     constraints, mass-normalised), disk friction cone, fixed sweep count;
  *   - semi-implicit Euler on the configuration (quaternion exponential map).
@@ -41,6 +42,8 @@ enum { ORC_PH_CPG = 0, ORC_PH_FK, ORC_PH_RNEA, ORC_PH_CRBA, ORC_PH_CHOL,
 
 enum { ORC_ST_NONFINITE = 1, ORC_ST_OVERFLOW = 2, ORC_ST_CHOL = 4 };
 
+enum { ORC_GEOM_BOX = 0, ORC_GEOM_SPHERE = 1 };
+
 typedef struct {
     int32_t nb;                 /* bodies, 1..32; body 0 is the root        */
     int32_t root_fixed;         /* 1: root pinned at (root_R, root_p)       */
@@ -56,6 +59,8 @@ typedef struct {
     double w_cpl[ORC_MAXB];     /* CPG coupling of hinge b to its parent    */
     double root_R[9];
     double root_p[3];
+    int32_t geom[ORC_MAXB];     /* ORC_GEOM_BOX or ORC_GEOM_SPHERE; a sphere
+                                   has radius half[b][0], centre com[b]     */
 } orc_model;
 
 typedef struct {
@@ -65,8 +70,8 @@ typedef struct {
     double soft_tau, soft_zeta, mu;
     int32_t contact_cap;
     double kp, kd, tau_max, theta_max, armature;
-    int32_t ground;             /* box/plane contacts on                    */
-    int32_t box_box;            /* box/box contacts on                      */
+    int32_t ground;             /* body/plane contacts on                   */
+    int32_t box_box;            /* body/body contacts inside a robot on     */
     int32_t actuate;            /* CPG + PD torques on                      */
     double max_correct_vel;     /* cap of the penetration recovery speed    */
     double min_cfm;             /* floor of a row's softness R [1/kg]       */

@@ -19,7 +19,12 @@ Populations:
   * ``quadrupeds`` -- core cube + 8 bricks in a fixed quadruped tree.
   * ``grammar``    -- random trees with 2..20 hinged bricks from a seeded
                        tree grammar, bricks on random free faces at random
-                       90-degree rotations, no self-overlap.
+                       90-degree rotations, no self-overlap; optionally some
+                       modules are balls (sphere geometry).
+  * ``box_and_ball`` -- a core cube with one hinged ball, dropped (the
+                       BOX_AND_BALL-like scene).
+  * ``rope``       -- a core cube trailing a chain of up to 25 bricks (the
+                       ARM_WITH_ROPE-like long chain within one warp).
 
 Body convention (shared reading of the model description):
   * body 0 is the core; its frame origin is the core centre.
@@ -43,6 +48,7 @@ MAX_HINGES = 20
 CORE_HALF_MM = 50
 BRICK_HALF_MM = 30
 DENSITY = 1000.0          # kg / m^3
+GEOM_BOX, GEOM_SPHERE = 0, 1
 START_CLEARANCE_MM = 5    # lowest vertex of a robot starts 5 mm above the plane
 
 # faces of a box in its own frame: +x, -x, +y, -y, +z, -z
@@ -91,6 +97,7 @@ class Population:
     exclude: np.ndarray       # (n, MAXB) uint32 bit j set: no contact with body j
     genome_face: np.ndarray   # (n, MAXB) int8 face of the parent each brick sits on
     genome_rot: np.ndarray    # (n, MAXB) int8 quarter-turn rotation of each brick
+    geom: np.ndarray          # (n, MAXB) int8 GEOM_BOX, or GEOM_SPHERE (radius half[..., 0])
 
     @property
     def nq(self) -> np.ndarray:
@@ -143,12 +150,18 @@ def _empty(kind: str, n: int) -> Population:
         exclude=np.zeros((n, MAXB), np.uint32),
         genome_face=np.full((n, MAXB), -1, np.int8),
         genome_rot=np.zeros((n, MAXB), np.int8),
+        geom=np.zeros((n, MAXB), np.int8),
     )
 
 
 def _box_mass(half_mm) -> float:
     side = 2.0 * np.asarray(half_mm, dtype=np.float64) / 1000.0
     return float(DENSITY * side[0] * side[1] * side[2])
+
+
+def _ball_mass(radius_mm) -> float:
+    r = float(radius_mm) / 1000.0
+    return float(DENSITY * 4.0 / 3.0 * np.pi * r ** 3)
 
 
 class _Lattice:
@@ -166,8 +179,11 @@ class _Lattice:
         self.R_fix = [np.eye(3, dtype=np.int64)]
         self.p_fix = [np.zeros(3, np.int64)]
         self.used_faces = [set()]
+        self.geom = [GEOM_BOX]
 
     def free_faces(self, b: int):
+        if self.geom[b] == GEOM_SPHERE:
+            return []  # a ball module is a leaf
         faces = [f for f in range(6) if f not in self.used_faces[b]]
         if b > 0:
             faces = [f for f in faces if f != _ATTACH_FACE]
@@ -195,8 +211,12 @@ class _Lattice:
                 return True
         return False
 
-    def add(self, p, face, r, placed):
+    def add(self, p, face, r, placed, geom=GEOM_BOX):
+        """Attach a module; a ball (geom GEOM_SPHERE) fills the brick's cube
+        (radius = the brick's half size) and its zero-pose overlap and touch
+        tests use that cube, a conservative bound."""
         R_fix, p_fix, R_w, origin, centre, half, com_local = placed
+        self.geom.append(geom)
         self.parent.append(p)
         self.face.append(face)
         self.rot.append(r)
@@ -222,8 +242,8 @@ class _Lattice:
 
     def lowest_vertex_mm(self) -> int:
         low = None
-        for c, h, R in zip(self.centre, self.half, self.R_world):
-            z = int(c[2] - (np.abs(R) @ h)[2])
+        for c, h, R, g in zip(self.centre, self.half, self.R_world, self.geom):
+            z = int(c[2] - (h[0] if g == GEOM_SPHERE else (np.abs(R) @ h)[2]))
             low = z if low is None else min(low, z)
         return low
 
@@ -238,7 +258,8 @@ def _write_robot(pop: Population, i: int, lat: _Lattice, rng, quad_weights=None)
         pop.p_fix[i, b] = lat.p_fix[b] / 1000.0
         pop.half[i, b] = lat.half[b] / 1000.0
         pop.com[i, b] = lat.com_local[b] / 1000.0
-        pop.mass[i, b] = _box_mass(lat.half[b])
+        pop.geom[i, b] = lat.geom[b]
+        pop.mass[i, b] = _ball_mass(lat.half[b][0]) if lat.geom[b] == GEOM_SPHERE else _box_mass(lat.half[b])
         pop.genome_face[i, b] = lat.face[b]
         pop.genome_rot[i, b] = lat.rot[b]
     for a, b in lat.touching_pairs():
@@ -294,8 +315,9 @@ def quadrupeds(n: int, seed: int = 2) -> Population:
     return pop
 
 
-def grammar_lattice(rng, n_hinges: int, max_tries: int = 100):
-    """Random tree: each brick goes on a random free face of a random body."""
+def grammar_lattice(rng, n_hinges: int, max_tries: int = 100, ball_p: float = 0.0):
+    """Random tree: each brick goes on a random free face of a random body;
+    with probability ``ball_p`` a module is a ball (a leaf) instead."""
     while True:
         lat = _Lattice()
         ok = True
@@ -311,7 +333,10 @@ def grammar_lattice(rng, n_hinges: int, max_tries: int = 100):
                 cand = lat.propose(p, face, r)
                 if lat.overlaps(cand[4], cand[5], cand[2]):
                     continue
-                lat.add(p, face, r, cand)
+                geom = GEOM_BOX
+                if ball_p > 0.0 and rng.uniform() < ball_p:
+                    geom = GEOM_SPHERE
+                lat.add(p, face, r, cand, geom)
                 placed = True
                 break
             if not placed:
@@ -321,13 +346,70 @@ def grammar_lattice(rng, n_hinges: int, max_tries: int = 100):
             return lat
 
 
-def grammar(n: int, seed: int = 3, hinges=(2, MAX_HINGES)) -> Population:
-    """Seeded tree-grammar robots with U{hinges} hinged bricks each."""
+def grammar(n: int, seed: int = 3, hinges=(2, MAX_HINGES), ball_p: float = 0.0) -> Population:
+    """Seeded tree-grammar robots with U{hinges} hinged modules each; a module
+    is a ball with probability ``ball_p`` (0: bricks only, the default)."""
     rng = np.random.default_rng(seed)
-    pop = _empty("grammar", n)
+    pop = _empty("grammar" if ball_p == 0.0 else "grammar_balls", n)
     for i in range(n):
         nh = int(rng.integers(hinges[0], hinges[1] + 1))
-        _write_robot(pop, i, grammar_lattice(rng, nh), rng)
+        _write_robot(pop, i, grammar_lattice(rng, nh, ball_p=ball_p), rng)
+    return pop
+
+
+def box_and_ball(n: int, seed: int = 4, z_range=(0.1, 0.5), vel_sigma=0.5) -> Population:
+    """A core cube with one ball module on a random face, hinged, dropped like
+    ``boxes``: height U[z_range] added to the resting clearance, orientation a
+    normalised N(0, I4) quaternion, root velocity components N(0, vel_sigma^2).
+    Sphere/plane and box/plane contacts (the ball and the core are adjacent
+    and never collide with each other)."""
+    rng = np.random.default_rng(seed)
+    pop = _empty("box_and_ball", n)
+    for i in range(n):
+        lat = _Lattice()
+        face = int(rng.integers(0, 6))
+        r = int(rng.integers(0, 4))
+        lat.add(0, face, r, lat.propose(0, face, r), GEOM_SPHERE)
+        _write_robot(pop, i, lat, rng)
+        quat = rng.normal(size=4)
+        quat /= np.linalg.norm(quat)
+        # clear of the plane in any orientation: the robot's bounding radius
+        reach = (CORE_HALF_MM * np.sqrt(3.0) + 2 * BRICK_HALF_MM + CORE_HALF_MM) / 1000.0
+        pop.q0[i, :7] = [0.0, 0.0, reach + rng.uniform(*z_range), *quat]
+        pop.v0[i, :6] = rng.normal(0.0, vel_sigma, size=6)
+    return pop
+
+
+def rope_lattice(links: int) -> _Lattice:
+    """Core cube with a straight chain of ``links`` bricks on its +x face,
+    each on the +x face of the one before, hinge axes alternating between
+    the bricks' y and z (quarter turn every second link)."""
+    lat = _Lattice()
+    p = 0
+    for k in range(links):
+        r = k % 2
+        lat.add(p, 0, r, lat.propose(p, 0, r))
+        p = len(lat.parent) - 1
+    return lat
+
+
+def rope(n: int, seed: int = 5, links: int = 25) -> Population:
+    """A long chain (up to 25 links, the per-robot body bound): a core cube
+    trailing a chain of bricks, dropped from U[0, 0.3] m above its resting
+    height, bent in the horizontal plane (vertical-axis hinges U[-0.3, 0.3],
+    the others straight), hinge rates N(0, 1).  Run with actuate=0 the chain
+    is passive (a rope); with the CPG on it is a snake."""
+    if not 1 <= links <= 25:
+        raise ValueError("links must be in 1..25")
+    rng = np.random.default_rng(seed)
+    pop = _empty("rope", n)
+    lat = rope_lattice(links)
+    vertical = np.array([k % 2 == 1 for k in range(links)])  # quarter-turned links
+    for i in range(n):
+        _write_robot(pop, i, lat, rng)
+        pop.q0[i, 2] += rng.uniform(0.0, 0.3)
+        pop.q0[i, 7:7 + links] = np.where(vertical, rng.uniform(-0.3, 0.3, size=links), 0.0)
+        pop.v0[i, 6:6 + links] = rng.normal(0.0, 1.0, size=links)
     return pop
 
 

@@ -34,6 +34,7 @@ def make_model(bodies, root_fixed=False, root_R=None, root_p=(0.0, 0.0, 0.0), w_
             m.half[b][k] = d.get("half", (0.03, 0.03, 0.03))[k]
             m.com[b][k] = d.get("com", (0, 0, 0))[k]
         m.mass[b] = d.get("mass", 0.216)
+        m.geom[b] = d.get("geom", 0)
         if w_int is not None:
             m.w_int[b] = w_int[b]
         if w_cpl is not None:
@@ -48,6 +49,11 @@ def make_model(bodies, root_fixed=False, root_R=None, root_p=(0.0, 0.0, 0.0), w_
 
 def single_box(half=0.05, mass=1.0):
     return make_model([dict(half=(half, half, half), mass=mass)])
+
+
+def single_ball(radius=0.05, mass=1.0, com=(0.0, 0.0, 0.0)):
+    """A free solid sphere (geometry 1): radius in half[0], centre at com."""
+    return make_model([dict(half=(radius, radius, radius), mass=mass, com=com, geom=1)])
 
 
 def brick_chain(n_links, root_fixed=True, root_p=(0.0, 0.0, 2.0)):

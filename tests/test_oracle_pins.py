@@ -642,6 +642,226 @@ def test_incline_stick_slide(alpha_deg, slides):
         assert abs(q[0]) < 0.02
 
 
+# ------------------------------------------------------------------ spheres
+def test_sphere_plane_contact_hand_placed():
+    """A tilted free ball whose centre sits off its frame origin: one contact
+    at the centre's foot, r below it, depth r - z_centre, normal +z; lifted
+    by 2 mm, none."""
+    R = H.rot("x", 0.7) @ H.rot("z", 0.3)
+    quat = _quat_of(R)
+    com = np.array([0.01, -0.02, 0.005])
+    m = H.single_ball(0.05, 1.0, com=tuple(com))
+    p0 = np.array([0.3, -0.2, 0.0])
+    centre = p0 + R @ com
+    p0[2] += 0.049 - centre[2]
+    centre = p0 + R @ com
+    c = O.contacts(m, free_q(tuple(p0), tuple(quat)), O.default_params())
+    assert len(c["a"]) == 1 and c["a"][0] == 0 and c["b"][0] == -1
+    assert abs(c["depth"][0] - 0.001) < 1e-12
+    assert np.allclose(c["n"][0], [0, 0, 1])
+    assert np.allclose(c["p"][0], centre - [0, 0, 0.05], atol=1e-12)
+    p0[2] += 0.002
+    assert len(O.contacts(m, free_q(tuple(p0), tuple(quat)), O.default_params())["a"]) == 0
+
+
+def _quat_of(R):
+    """Unit quaternion (w, x, y, z) of a rotation matrix (Shepperd's method)."""
+    t = np.trace(R)
+    if t > 0:
+        w = np.sqrt(1 + t) / 2
+        return np.array([w, (R[2, 1] - R[1, 2]) / (4 * w), (R[0, 2] - R[2, 0]) / (4 * w), (R[1, 0] - R[0, 1]) / (4 * w)])
+    i = int(np.argmax(np.diag(R)))
+    j, k = (i + 1) % 3, (i + 2) % 3
+    x = np.sqrt(1 + R[i, i] - R[j, j] - R[k, k]) / 2
+    q = np.zeros(4)
+    q[0] = (R[k, j] - R[j, k]) / (4 * x)
+    q[1 + i] = x
+    q[1 + j] = (R[j, i] + R[i, j]) / (4 * x)
+    q[1 + k] = (R[k, i] + R[i, k]) / (4 * x)
+    return q
+
+
+def test_resting_ball_steady_penetration():
+    """A ball at rest has one contact straight below its centre, so the row
+    has A = 1/m (no lever arm), impulse m g dt and steady depth
+    d* = kappa A lambda dt / ERP."""
+    mass = 1000.0 * 4.0 / 3.0 * np.pi * 0.05 ** 3
+    m = H.single_ball(0.05, mass)
+    p = O.default_params()
+    q, v, _, st, _ = O.run(m, free_q((0.0, 0.0, 0.0501)), np.zeros(6), np.zeros(2), 3000, prm=p)
+    omg = 2 * np.pi / p.soft_tau
+    kden = p.dt * omg * omg + 2 * p.soft_zeta * omg
+    erp = p.dt * omg * omg / kden
+    kappa = 1.0 / (p.dt * kden)
+    A = 1.0 / mass
+    assert kappa * A > p.min_cfm
+    lam = mass * G * p.dt
+    dstar = kappa * A * lam * p.dt / erp
+    assert st == 0
+    assert abs(q[2] - (0.05 - dstar)) < 1e-7
+    assert np.abs(v).max() < 1e-6
+
+
+@pytest.mark.parametrize("alpha_deg,mu,rolls", [(20.0, 0.5, True), (40.0, 0.1, False)])
+def test_ball_on_incline_rolls_or_slides(alpha_deg, mu, rolls):
+    """Tilted gravity on a flat plane = an incline.  A solid ball (I = 2/5 m r^2)
+    rolls without slipping iff mu >= (2/7) tan(alpha), with acceleration
+    (5/7) g sin(alpha) and v = omega r; otherwise it slides with acceleration
+    g (sin a - mu cos a) while friction spins it up at 5 mu g cos(a) / (2 r).
+    A wrong moment of inertia, lever arm or contact point fails both."""
+    a = np.radians(alpha_deg)
+    r = 0.05
+    assert (mu >= 2.0 / 7.0 * np.tan(a)) == rolls
+    p = O.default_params(mu=mu, gravity=(G * np.sin(a), 0.0, -G * np.cos(a)))
+    m = H.single_ball(r, 0.5)
+    q = free_q((0.0, 0.0, r - 1e-4))
+    q, v, _, _, _ = O.run(m, q, np.zeros(6), np.zeros(2), 100, prm=p)
+    v0, w0 = v[0], v[4]
+    t = 400 * p.dt
+    q, v, _, st, _ = O.run(m, q, v, np.zeros(2), 400, prm=p)
+    assert st == 0
+    acc = (v[0] - v0) / t
+    spin = (v[4] - w0) / t   # body y spin, world y while the ball turns about y
+    if rolls:
+        assert abs(acc - 5.0 / 7.0 * G * np.sin(a)) < 0.01 * G * np.sin(a)
+        assert abs(v[0] - v[4] * r) < 0.01 * abs(v[0])
+    else:
+        assert abs(acc - G * (np.sin(a) - mu * np.cos(a))) < 0.01 * G * np.sin(a)
+        assert abs(spin - 5.0 * mu * G * np.cos(a) / (2.0 * r)) < 0.01 * 5.0 * mu * G * np.cos(a) / (2.0 * r)
+        assert v[0] - v[4] * r > 0.1
+
+
+def _ball_and_box(pa, Ra, pb, Rb, ga, gb, ha=0.03, hb=0.03):
+    """Fixed root far away with two children (geometry ga, gb) placed by their
+    joint frames; both centred on their frame origins."""
+    bodies = [dict(half=(0.05, 0.05, 0.05), mass=1.0),
+              dict(parent=0, axis=1, R_fix=Ra, p_fix=pa, half=(ha, ha, ha), geom=ga),
+              dict(parent=0, axis=1, R_fix=Rb, p_fix=pb, half=(hb, hb, hb), geom=gb)]
+    return H.make_model(bodies, root_fixed=True, root_p=(0.0, 0.0, 5.0))
+
+
+def _box_surface(c, R, h, k=120):
+    """Points on a box's surface, k x k per face."""
+    g = np.linspace(-1.0, 1.0, k)
+    u, w = np.meshgrid(g, g)
+    u, w = u.ravel(), w.ravel()
+    pts = []
+    for ax in range(3):
+        for sg in (-1.0, 1.0):
+            loc = np.zeros((u.size, 3))
+            loc[:, ax] = sg
+            loc[:, (ax + 1) % 3] = u
+            loc[:, (ax + 2) % 3] = w
+            pts.append(loc * h)
+    return c + np.concatenate(pts) @ R.T
+
+
+def test_sphere_sphere_contact_against_sampling():
+    """Two balls: a contact iff sampled points of one lie inside the other;
+    the depth is the overlap of their extents along the returned normal (a
+    support-function check), the normal is unit, and the point lies on the
+    centre line midway between the two surfaces."""
+    rng = np.random.default_rng(11)
+    u = rng.normal(size=(20000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    u *= rng.uniform(0, 1, size=(20000, 1)) ** (1 / 3)
+    seen = [0, 0]
+    for _ in range(40):
+        ca = np.array([0.0, 1.0, 0.0])
+        cb = ca + rng.normal(0, 0.035, 3)
+        ra, rb = 0.03, rng.uniform(0.015, 0.03)
+        m = _ball_and_box(ca, np.eye(3), cb, H.rot("z", 1.0), 1, 1, 0.03, rb)
+        c = O.contacts(m, np.zeros(2), O.default_params(ground=0))
+        overlap = np.any(np.linalg.norm(ca + ra * u - cb, axis=1) <= rb)
+        if len(c["a"]) == 0:
+            assert not overlap
+            seen[0] += 1
+            continue
+        assert len(c["a"]) == 1 and (c["a"][0], c["b"][0]) == (1, 2)
+        n = c["n"][0]
+        assert abs(np.linalg.norm(n) - 1) < 1e-12
+        # support functions along n (from b towards a): a reaches down to
+        # ca.n - ra, b reaches up to cb.n + rb
+        assert abs((cb @ n + rb) - (ca @ n - ra) - c["depth"][0]) < 1e-12
+        assert np.allclose(np.cross(n, ca - cb), 0, atol=1e-12) and n @ (ca - cb) > 0
+        mid = 0.5 * ((ca + [0, 0, 5.0] - ra * n) + (cb + [0, 0, 5.0] + rb * n))
+        assert np.allclose(c["p"][0], mid, atol=1e-12)
+        if c["depth"][0] > 0.003:
+            assert overlap
+        seen[1] += 1
+    assert seen[0] > 5 and seen[1] > 5
+
+
+@pytest.mark.parametrize("ball_first", [True, False])
+def test_sphere_box_contact_against_surface_sampling(ball_first):
+    """Ball against a rotated box, centre outside and inside the box.  The
+    distance from the centre to the box surface, found by sampling the six
+    faces densely, gives the depth (r - distance outside, r + distance
+    inside) and, through the nearest sample, the normal's direction; the
+    normal always points from the higher-index body to the lower."""
+    rng = np.random.default_rng(12 if ball_first else 13)
+    hb = np.array([0.03, 0.02, 0.025])
+    r = 0.02
+    seen = [0, 0, 0]
+    for _ in range(40):
+        Rx = H.rot("z", rng.uniform(0, 6)) @ H.rot("x", rng.uniform(0, 6))
+        cx = np.array([0.0, 1.0, 0.0])
+        cs = cx + rng.normal(0, 0.03, 3)
+        if ball_first:
+            m = _ball_and_box(cs, np.eye(3), cx, Rx, 1, 0, r, 0.03)
+        else:
+            m = _ball_and_box(cx, Rx, cs, np.eye(3), 0, 1, 0.03, r)
+        for b in (1, 2):
+            if m.geom[b] == 0:
+                for k in range(3):
+                    m.half[b][k] = hb[k]
+        c = O.contacts(m, np.zeros(2), O.default_params(ground=0))
+        surf = _box_surface(cx, Rx, hb)
+        dist = np.linalg.norm(surf - cs, axis=1)
+        j = int(np.argmin(dist))
+        inside = np.all(np.abs(Rx.T @ (cs - cx)) <= hb)
+        depth = r + dist[j] if inside else r - dist[j]
+        if len(c["a"]) == 0:
+            assert depth < 1e-3
+            seen[0] += 1
+            continue
+        assert len(c["a"]) == 1 and (c["a"][0], c["b"][0]) == (1, 2)
+        assert abs(c["depth"][0] - depth) < 1e-3
+        n = c["n"][0]
+        assert abs(np.linalg.norm(n) - 1) < 1e-12
+        out_dir = (cs - surf[j]) / dist[j] * (-1.0 if inside else 1.0)  # box -> ball
+        n_box_to_ball = n if ball_first else -n
+        if dist[j] > 0.004:  # the sample grid (0.5 mm) blurs directions closer in
+            assert n_box_to_ball @ out_dir > 0.98
+        # the point lies between the box surface and the ball's deepest point
+        p = c["p"][0] - [0, 0, 5.0]
+        deepest = cs - r * n_box_to_ball
+        assert np.linalg.norm(p - 0.5 * (deepest + surf[j])) < 2e-3
+        seen[2 if inside else 1] += 1
+    assert seen[0] > 3 and seen[1] > 5 and seen[2] > 2
+
+
+def test_ball_modules_keep_momentum_in_free_flight():
+    """A grammar robot with ball modules in free flight (gravity off, no
+    contacts): linear momentum stays zero-change and the ball's own spin
+    about its hinge costs no energy beyond the integrator's drift."""
+    pop = P.grammar(40, seed=21, ball_p=0.5)
+    i = int(np.argmax([(pop.geom[k] == 1).sum() for k in range(pop.n)]))
+    assert (pop.geom[i] == 1).sum() >= 2
+    m = O.model_from_population(pop, i)
+    assert m.geom[0] == 0 and sum(m.geom[b] for b in range(m.nb)) >= 2
+    p = prm(gravity=(0.0, 0.0, 0.0))
+    q, v, s = P.random_state(pop.subset([i]), seed=5)
+    nq, nv = O.nq(m), O.nv(m)
+    q0, v0 = q[0, :nq].copy(), v[0, :nv].copy()
+    M0 = O.mass_matrix(m, q0, p)
+    e0 = 0.5 * v0 @ M0 @ v0
+    q1, v1, _, st, _ = O.run(m, q0, v0, s[0], 200, prm=p)
+    assert st == 0
+    e1 = 0.5 * v1 @ O.mass_matrix(m, q1, p) @ v1
+    assert abs(e1 - e0) < 0.02 * e0
+
+
 # ---------------------------------------------------------------------- CPG
 def test_cpg_single_oscillator_norm_growth():
     """Explicit Euler of a 2x2 rotation generator: |s_n| = |s_0| (1 + dt^2 w^2)^(n/2)."""
