@@ -88,8 +88,8 @@ typedef struct {
     float kp, kd, tau_max;    /* PD servo gains and torque limit             */
     float theta_max;          /* CPG amplitude [rad]                         */
     float armature;           /* rotor inertia added on hinge diagonals      */
-    int32_t ground;           /* 1: box/plane contacts                       */
-    int32_t box_box;          /* 1: box/box contacts inside a robot          */
+    int32_t ground;           /* 1: body/plane contacts                      */
+    int32_t box_box;          /* 1: body/body contacts inside a robot        */
     int32_t actuate;          /* 1: CPG + PD torques                         */
     float max_correct_vel;    /* cap of the penetration recovery speed [m/s] */
     int32_t device;           /* CUDA device ordinal                         */
@@ -115,13 +115,23 @@ typedef struct {
     const uint32_t* exclude;      /* bit j: body never collides with body j   */
     const float* joint_frame;     /* 12 per body: R (3x3 row-major), p (3):
                                      body frame at zero angle in its parent  */
-    const float* half_size;       /* 3 per body: box half extents [m]         */
-    const float* box_center;      /* 3 per body: box centre in body frame [m] */
-    const float* mass;            /* [kg]; inertia is that of a solid box     */
+    const float* half_size;       /* 3 per body: box half extents [m]; a
+                                     sphere has all three equal its radius   */
+    const float* box_center;      /* 3 per body: box or sphere centre in the
+                                     body frame [m]                          */
+    const float* mass;            /* [kg]; inertia is that of the solid shape */
     const float* cpg_w_internal;  /* per body: oscillator weight of hinge b   */
     const float* cpg_w_couple;    /* per body: coupling of hinge b to the
                                      hinge of its parent (0 if parent = 0)   */
+    const int8_t* geom;           /* per body: SIM_GEOM_BOX or SIM_GEOM_SPHERE;
+                                     NULL: every body is a box               */
 } sim_variant_desc;
+
+/* body geometries: a box meets the plane at its vertices and other bodies by
+ * the separating-axis test; a sphere meets the plane, a box or a sphere at
+ * one point (the deepest, midway between the two surfaces) */
+#define SIM_GEOM_BOX 0
+#define SIM_GEOM_SPHERE 1
 
 typedef struct {
     double contacts;          /* sum over variants and steps of contacts     */
@@ -235,10 +245,11 @@ int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
  * Device layout expected in *pop (all device pointers, caller-owned):
  *   model_f  n x SIM_MODEL_NF x 32 floats, [variant][field][body slot]:
  *            joint frame R (9, row-major), joint frame p (3), half size (3),
- *            box centre (3), mass, principal inertia about the box centre
- *            (3: m(hy^2+hz^2)/3, m(hx^2+hz^2)/3, m(hx^2+hy^2)/3), CPG weight,
- *            CPG coupling, bounding radius |half size|; slots >= n_bodies
- *            hold R = identity and zeros.
+ *            box centre (3), mass, principal inertia about the centre
+ *            (3: box m(hy^2+hz^2)/3, m(hx^2+hz^2)/3, m(hx^2+hy^2)/3; sphere
+ *            2 m r^2 / 5 each), CPG weight, CPG coupling, bounding radius
+ *            (box |half size|, sphere r), geometry (0.0 box, 1.0 sphere);
+ *            slots >= n_bodies hold R = identity and zeros.
  *   model_i  n x SIM_MODEL_NI x 32 int32: parent (-1 for body 0 and unused
  *            slots), hinge axis, path mask (bit j for every body on the path
  *            from body 0 to this body, both ends included), child mask, depth
@@ -252,7 +263,7 @@ int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
  * Returns SIM_OK, SIM_EINVAL (bad argument; sim_last_error(NULL) says which)
  * or SIM_ECUDA. */
 #define SIM_NOALLOC_MAX_VARIANTS 64
-#define SIM_MODEL_NF 25
+#define SIM_MODEL_NF 26
 #define SIM_MODEL_NI 5
 
 typedef struct {

@@ -278,22 +278,27 @@ bool step_robot(const Robot& m, const uint16_t* pairs, const StepParams& P, floa
     for (int j = 0; j < nv; ++j) w.vfree[j] = v[j] + dt * t[j];
   }
 
-  // ---- 6. contact candidates: box/plane vertices, then box/box pairs
+  // ---- 6. contact candidates: body/plane points, then body/body pairs
   int ncand = 0;
   if (P.ground) {
     const float up[3] = {0.f, 0.f, 1.f};
     for (int b = 0; b < nb; ++b) {
-      const float h0 = fld(F_HALF, b), h1 = fld(F_HALF + 1, b), h2 = fld(F_HALF + 2, b);
+      // a box's 8 vertices; a sphere's lowest point (no half-size offsets, r below)
+      const bool sph = fld(F_GEOM, b) != 0.f;
+      const float hr = fld(F_HALF, b);
+      const float h0 = sph ? 0.f : hr, h1 = sph ? 0.f : fld(F_HALF + 1, b), h2 = sph ? 0.f : fld(F_HALF + 2, b);
+      const float drop = sph ? hr : 0.f;
       const float c0 = fld(F_COM, b), c1 = fld(F_COM + 1, b), c2 = fld(F_COM + 2, b);
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < (sph ? 1 : 8); ++k) {
         const float l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
         const double h = (double)q[2] + (w.hzb[b] + (w.hz[0][b] * (double)l0 + w.hz[1][b] * (double)l1 +
-                                                     w.hz[2][b] * (double)l2));
+                                                     w.hz[2][b] * (double)l2)) - (double)drop;
         if (!(h < 0.0)) continue;
         if (ncand < kCand) {
           float pr[3];
           for (int a = 0; a < 3; ++a)
             pr[a] = w.r[a][b] + (w.R[3 * a][b] * l0 + w.R[3 * a + 1][b] * l1 + w.R[3 * a + 2][b] * l2);
+          pr[2] -= drop;
           put_candidate(&w.cand[0][0], ncand, pr, up, (float)(-h), b, 255);
         }
         ++ncand;
@@ -309,7 +314,7 @@ bool step_robot(const Robot& m, const uint16_t* pairs, const StepParams& P, floa
       const float dx = w.c[0][b] - w.c[0][a], dy = w.c[1][b] - w.c[1][a], dz = w.c[2][b] - w.c[2][a];
       const float rr = fld(F_RAD, a) + fld(F_RAD, b);
       if (!(dx * dx + dy * dy + dz * dz <= rr * rr)) continue;
-      const int cnt = box_box_lane(w.R, w.c, F, a, b, stage);
+      const int cnt = body_pair_lane(w.R, w.c, F, a, b, stage);
       for (int t = 0; t < cnt; ++t) {
         if (ncand + t < kCand) std::memcpy(w.cand[ncand + t], stage + t * kCandW, kCandW * sizeof(float));
       }

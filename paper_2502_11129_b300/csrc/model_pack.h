@@ -3,7 +3,7 @@
 //
 // Layout per packed robot k (robots sorted by body count, largest first,
 // stable): float fields [NF][32 body slots], int fields [NI][32], meta
-// (bodies, tree depth, pair count, pair offset) and the list of box/box
+// (bodies, tree depth, pair count, pair offset) and the list of body/body
 // candidate pairs (a < b, a not the parent of b, not excluded), each packed
 // as (a << 8) | b.
 #pragma once
@@ -59,7 +59,10 @@ inline std::string validate_population(const sim_variant_desc* v, int n, const c
           !finite_all(d.box_center + 3 * b, 3) || !(d.half_size[3 * b] > 0.f) || !(d.half_size[3 * b + 1] > 0.f) ||
           !(d.half_size[3 * b + 2] > 0.f) ||
           (d.cpg_w_internal && !std::isfinite(d.cpg_w_internal[b])) ||
-          (d.cpg_w_couple && !std::isfinite(d.cpg_w_couple[b]))) {
+          (d.cpg_w_couple && !std::isfinite(d.cpg_w_couple[b])) ||
+          (d.geom && d.geom[b] != SIM_GEOM_BOX && d.geom[b] != SIM_GEOM_SPHERE) ||
+          (d.geom && d.geom[b] == SIM_GEOM_SPHERE &&
+           (d.half_size[3 * b + 1] != d.half_size[3 * b] || d.half_size[3 * b + 2] != d.half_size[3 * b]))) {
         snprintf(buf, sizeof buf, ": variant %d body %d is invalid", i, b);
         return std::string(who) + buf;
       }
@@ -120,13 +123,19 @@ inline void pack_population(const sim_variant_desc* v, int n, PackedPopulation& 
       }
       const double m = d.mass[b];
       const double hx = d.half_size[3 * b], hy = d.half_size[3 * b + 1], hz = d.half_size[3 * b + 2];
+      const bool sphere = d.geom && d.geom[b] == SIM_GEOM_SPHERE;
       F[b3::F_MASS * 32 + b] = d.mass[b];
-      F[(b3::F_ID + 0) * 32 + b] = (float)(m * (hy * hy + hz * hz) / 3.0);
-      F[(b3::F_ID + 1) * 32 + b] = (float)(m * (hx * hx + hz * hz) / 3.0);
-      F[(b3::F_ID + 2) * 32 + b] = (float)(m * (hx * hx + hy * hy) / 3.0);
+      if (sphere) {  // solid sphere: 2 m r^2 / 5 about every axis
+        for (int t = 0; t < 3; ++t) F[(b3::F_ID + t) * 32 + b] = (float)(0.4 * m * hx * hx);
+      } else {       // solid box: m (h_j^2 + h_k^2) / 3
+        F[(b3::F_ID + 0) * 32 + b] = (float)(m * (hy * hy + hz * hz) / 3.0);
+        F[(b3::F_ID + 1) * 32 + b] = (float)(m * (hx * hx + hz * hz) / 3.0);
+        F[(b3::F_ID + 2) * 32 + b] = (float)(m * (hx * hx + hy * hy) / 3.0);
+      }
       F[b3::F_WINT * 32 + b] = d.cpg_w_internal ? d.cpg_w_internal[b] : 0.f;
       F[b3::F_WCPL * 32 + b] = d.cpg_w_couple ? d.cpg_w_couple[b] : 0.f;
-      F[b3::F_RAD * 32 + b] = (float)std::sqrt(hx * hx + hy * hy + hz * hz);
+      F[b3::F_RAD * 32 + b] = sphere ? (float)hx : (float)std::sqrt(hx * hx + hy * hy + hz * hz);
+      F[b3::F_GEOM * 32 + b] = sphere ? 1.f : 0.f;
     }
     const int off = (int)pairs.size();
     for (int a = 0; a < nb; ++a)

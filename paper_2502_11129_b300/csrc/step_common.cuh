@@ -1,7 +1,7 @@
 // step_common.cuh -- pieces of the population step shared by the GPU step
 // kernel and the host (CPU) engine: model layout, step constants, spatial
-// algebra, the box/box narrow phase, the FP64 sine / cosine and the contact
-// tangent basis.  Everything here is __host__ __device__: the same source
+// algebra, the box/box and sphere narrow phases, the FP64 sine / cosine and
+// the contact tangent basis.  Everything here is __host__ __device__: the same source
 // gives both engines the same geometry decisions.
 #pragma once
 #include <cuda_runtime.h>
@@ -32,8 +32,9 @@ enum : int {
   F_ID = 19,     // 3: principal inertia about the box centre
   F_WINT = 22,
   F_WCPL = 23,
-  F_RAD = 24,    // bounding-sphere radius
-  NF = 25
+  F_RAD = 24,    // bounding-sphere radius (a sphere's own radius)
+  F_GEOM = 25,   // 0 box, 1 sphere (radius F_HALF)
+  NF = 26
 };
 // per-variant int model fields, [field][32 body slots]
 enum : int { I_PARENT = 0, I_AXIS, I_PATH, I_CHILD, I_DEPTH, NI = 5 };
@@ -311,6 +312,83 @@ __host__ __device__ __noinline__ int box_box_lane(const float (*RR)[32], const f
   out[6] = ebest;
   out[7] = int_bits_as_float(ab);
   return 1;
+}
+
+// Sphere/box or sphere/sphere contact of one body pair a < b (at least one a
+// sphere) on one lane: one row at most, written to `out` (candidate layout);
+// returns 0 or 1.  The point lies midway between the two surfaces' deepest
+// points along the normal; normals point from b to a.  Sphere/sphere: normal
+// along the centre difference, depth r_a + r_b - |d|.  Sphere/box: Q = the
+// sphere centre C clamped to the box in box axes; C outside the box: normal
+// along C - Q, depth r - |C - Q|; C inside: the nearest face's normal
+// (smallest h_k - |C_k|, ties to the lowest k), depth r + h_k - |C_k|.
+__host__ __device__ __noinline__ int sphere_pair_lane(const float (*RR)[32], const float (*CC)[32],
+                                                      const float* __restrict__ F, int a, int b, float* out) {
+  const bool sa = F[F_GEOM * 32 + a] != 0.f, sb = F[F_GEOM * 32 + b] != 0.f;
+  float n[3], p[3], depth;
+  if (sa && sb) {
+    const float ra = F[F_HALF * 32 + a], rb = F[F_HALF * 32 + b];
+    const float d[3] = {CC[0][a] - CC[0][b], CC[1][a] - CC[1][b], CC[2][a] - CC[2][b]};
+    const float dist = sqrtf(dot3(d, d));
+    depth = ra + rb - dist;
+    if (!(depth > 0.f) || !(dist > 0.f)) return 0;
+    for (int k = 0; k < 3; ++k) {
+      n[k] = d[k] / dist;
+      p[k] = 0.5f * ((CC[k][a] - ra * n[k]) + (CC[k][b] + rb * n[k]));
+    }
+  } else {
+    const int is = sa ? a : b, ix = sa ? b : a;  // the sphere and the box
+    const float r = F[F_HALF * 32 + is];
+    float h[3], D[3], l[3], q[3], e[3];
+    for (int k = 0; k < 3; ++k) {
+      h[k] = F[(F_HALF + k) * 32 + ix];
+      D[k] = CC[k][is] - CC[k][ix];
+    }
+    for (int k = 0; k < 3; ++k) {
+      float ax[3];
+      axis_of(RR, ix, k, ax);
+      l[k] = dot3(ax, D);
+      q[k] = fminf(fmaxf(l[k], -h[k]), h[k]);
+      e[k] = l[k] - q[k];
+    }
+    const float e2 = dot3(e, e);
+    float nl[3], pl[3];
+    if (e2 > 0.f) {
+      const float dist = sqrtf(e2);
+      depth = r - dist;
+      if (!(depth > 0.f)) return 0;
+      for (int k = 0; k < 3; ++k) {
+        nl[k] = e[k] / dist;
+        pl[k] = q[k] - 0.5f * depth * nl[k];
+      }
+    } else {
+      int kk = 0;
+      float pen = h[0] - fabsf(l[0]);
+      for (int k = 1; k < 3; ++k) {
+        const float pk = h[k] - fabsf(l[k]);
+        if (pk < pen) { pen = pk; kk = k; }
+      }
+      depth = r + pen;
+      for (int k = 0; k < 3; ++k) nl[k] = k == kk ? (l[kk] >= 0.f ? 1.f : -1.f) : 0.f;
+      for (int k = 0; k < 3; ++k) pl[k] = l[k] + 0.5f * (pen - r) * nl[k];
+    }
+    const float sg = is == a ? 1.f : -1.f;  // box-to-sphere, flipped when the sphere is b
+    for (int k = 0; k < 3; ++k) {
+      n[k] = sg * (RR[3 * k][ix] * nl[0] + RR[3 * k + 1][ix] * nl[1] + RR[3 * k + 2][ix] * nl[2]);
+      p[k] = CC[k][ix] + (RR[3 * k][ix] * pl[0] + RR[3 * k + 1][ix] * pl[1] + RR[3 * k + 2][ix] * pl[2]);
+    }
+  }
+  put_candidate(out, 0, p, n, depth, a, b);
+  return 1;
+}
+
+// Narrow phase of one body pair a < b on one lane, by geometry: box/box, or
+// sphere/box and sphere/sphere.  Rows to `out` (candidate layout); returns
+// their count.
+__host__ __device__ __noinline__ int body_pair_lane(const float (*RR)[32], const float (*CC)[32],
+                                                    const float* __restrict__ F, int a, int b, float* out) {
+  if (F[F_GEOM * 32 + a] != 0.f || F[F_GEOM * 32 + b] != 0.f) return sphere_pair_lane(RR, CC, F, a, b, out);
+  return box_box_lane(RR, CC, F, a, b, out);
 }
 
 // Double-precision sine and cosine of one argument, compact enough to live in

@@ -507,16 +507,22 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     // ---------------- 6. contact candidates
     int ncand = 0;
     if (P.ground) {
+      // a box's 8 vertices (bit i of k: + half size along axis i); a
+      // sphere's lowest point: k = 0 with no half-size offsets, r below
       unsigned mask8 = 0;
-      const float h0 = fld(F_HALF), h1 = fld(F_HALF + 1), h2 = fld(F_HALF + 2);
+      const bool sph = fld(F_GEOM) != 0.f;
+      const float hr = fld(F_HALF);
+      const float h0 = sph ? 0.f : hr, h1 = sph ? 0.f : fld(F_HALF + 1), h2 = sph ? 0.f : fld(F_HALF + 2);
+      const float drop = sph ? hr : 0.f;
       const float c0 = fld(F_COM), c1 = fld(F_COM + 1), c2 = fld(F_COM + 2);
       auto vheight = [&](int k) {
         const double l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
-        return (double)p0z + (hzb + (hz0 * l0 + hz1 * l1 + hz2 * l2));
+        return (double)p0z + (hzb + (hz0 * l0 + hz1 * l1 + hz2 * l2)) - (double)drop;
       };
       if (body) {
+        const int nvert = sph ? 1 : 8;
 #pragma unroll 1
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < nvert; ++k)
           if (vheight(k) < 0.0) mask8 |= 1u << k;
       }
       const int cnt = __popc(mask8);
@@ -534,6 +540,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         float pr[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) pr[a] = r[a] + (R[3 * a] * l0 + R[3 * a + 1] * l1 + R[3 * a + 2] * l2);
+        pr[2] -= drop;
         if (off < kCand) put_candidate(cand, off, pr, up, (float)(-vheight(k)), lane, 255);
         ++off;
       }
@@ -573,7 +580,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         int cnt = 0;
         if (qi < nnear) {
           const unsigned pr = sm.nearp[qi];
-          cnt = box_box_lane(sm.R, sm.c, F, (int)(pr >> 8), (int)(pr & 0xffu), stage);
+          cnt = body_pair_lane(sm.R, sm.c, F, (int)(pr >> 8), (int)(pr & 0xffu), stage);
         }
         int incl = cnt;
 #pragma unroll

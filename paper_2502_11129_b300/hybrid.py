@@ -193,7 +193,7 @@ def main():
     from . import cpu as CP
     from . import sweeps as SW
     ap = argparse.ArgumentParser()
-    ap.add_argument("--scene", choices=["box", "quadruped", "grammar"], default="grammar")
+    ap.add_argument("--scene", choices=list(SW.SCENES), default="grammar")
     ap.add_argument("--variants", type=int, nargs="*", default=[128, 512, 2048, 8192])
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--reps", type=int, default=3)
@@ -201,8 +201,9 @@ def main():
     a = ap.parse_args()
     rows = []
     for n in a.variants:
-        r = hybrid_point(SW.scene(a.scene, n), a.steps, lambda: S.Sim(), lambda: CP.CpuSim(threads=a.threads),
-                         a.reps)
+        cfg = SW.SCENE_CFG.get(a.scene, {})
+        r = hybrid_point(SW.scene(a.scene, n), a.steps, lambda: S.Sim(**cfg),
+                         lambda: CP.CpuSim(threads=a.threads, **cfg), a.reps)
         r["scene"] = a.scene
         rows.append(r)
         print(json.dumps(r), flush=True)

@@ -46,7 +46,7 @@ class VariantDesc(C.Structure):
         ("exclude", C.POINTER(C.c_uint32)), ("joint_frame", C.POINTER(C.c_float)),
         ("half_size", C.POINTER(C.c_float)), ("box_center", C.POINTER(C.c_float)),
         ("mass", C.POINTER(C.c_float)), ("cpg_w_internal", C.POINTER(C.c_float)),
-        ("cpg_w_couple", C.POINTER(C.c_float)),
+        ("cpg_w_couple", C.POINTER(C.c_float)), ("geom", C.POINTER(C.c_int8)),
     ]
 
 
@@ -124,6 +124,7 @@ class Population32:
         self.mass = np.ascontiguousarray(pop.mass, dtype=np.float32)
         self.w_int = np.ascontiguousarray(pop.w_int, dtype=np.float32)
         self.w_cpl = np.ascontiguousarray(pop.w_cpl, dtype=np.float32)
+        self.geom = np.ascontiguousarray(pop.geom, dtype=np.int8)
         self.descs = (VariantDesc * n)()
         f = C.POINTER(C.c_float)
         for i in range(n):
@@ -138,6 +139,7 @@ class Population32:
             d.mass = self.mass[i].ctypes.data_as(f)
             d.cpg_w_internal = self.w_int[i].ctypes.data_as(f)
             d.cpg_w_couple = self.w_cpl[i].ctypes.data_as(f)
+            d.geom = self.geom[i].ctypes.data_as(C.POINTER(C.c_int8))
 
 
 def state_rows(pop: popmod.Population, q, v, s):

@@ -10,8 +10,11 @@ simulator:
     python -m paper_2502_11129_b300.sweeps --sweep steps --scene grammar
 
 Scenes: ``box`` (one free 0.1 m cube per variant, the BOX-like scene),
-``quadruped`` and ``grammar`` (tree-grammar robots with 2..20 hinges).  Large
-quadruped and grammar populations repeat a base population of 4096 distinct
+``box_and_ball`` (a cube with one hinged ball, the BOX_AND_BALL-like scene),
+``rope`` (a cube trailing a passive 25-link chain, the ARM_WITH_ROPE-like
+scene), ``quadruped``, ``grammar`` (tree-grammar robots with 2..20 hinges)
+and ``grammar_balls`` (the same with 30 % of the modules balls).  Large
+populations other than ``box`` repeat a base population of 4096 distinct
 robots (generating robots is host work that the sweep does not time).
 
 Each point: build the population and the simulator, one untimed call that
@@ -42,15 +45,27 @@ BASE_ROBOTS = 4096  # distinct robots behind large quadruped / grammar populatio
 _BASE = {}
 
 
+_MAKERS = {
+    "quadruped": lambda n, seed: P.quadrupeds(n, seed=seed),
+    "grammar": lambda n, seed: P.grammar(n, seed=seed),
+    "grammar_balls": lambda n, seed: P.grammar(n, seed=seed, ball_p=0.3),
+    "box_and_ball": lambda n, seed: P.box_and_ball(n, seed=seed),
+    "rope": lambda n, seed: P.rope(n, seed=seed),
+}
+SCENES = ("box",) + tuple(_MAKERS)
+# simulator settings a scene runs with (a rope is a passive chain)
+SCENE_CFG = {"rope": dict(actuate=0)}
+
+
 def scene(name: str, n: int, seed: int = 1) -> P.Population:
     if name == "box":
         return P.boxes(n, seed=seed)
-    if name not in ("quadruped", "grammar"):
+    if name not in _MAKERS:
         raise ValueError(f"unknown scene {name!r}")
     base_n = min(n, BASE_ROBOTS)
     key = (name, seed)
     if key not in _BASE or _BASE[key].n < base_n:
-        _BASE[key] = P.quadrupeds(base_n, seed=seed) if name == "quadruped" else P.grammar(base_n, seed=seed)
+        _BASE[key] = _MAKERS[name](base_n, seed)
     base = _BASE[key]
     return base.subset(np.arange(n) % base.n)
 
@@ -85,14 +100,14 @@ def sweep(kind: str, scene_name: str, values=None, reps: int = 3, seed: int = 1,
     rows = []
     if kind == "variants":
         for n in values or PAPER_VARIANTS:
-            r = time_point(scene(scene_name, n, seed), 1000, reps)
+            r = time_point(scene(scene_name, n, seed), 1000, reps, **SCENE_CFG.get(scene_name, {}))
             r["scene"] = scene_name
             rows.append(r)
             log(json.dumps(r))
     elif kind == "steps":
         pop = scene(scene_name, 128, seed)
         for s in values or PAPER_STEPS:
-            r = time_point(pop, s, reps)
+            r = time_point(pop, s, reps, **SCENE_CFG.get(scene_name, {}))
             r["scene"] = scene_name
             rows.append(r)
             log(json.dumps(r))
@@ -112,7 +127,7 @@ def table(rows) -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--sweep", choices=["variants", "steps"], default="variants")
-    ap.add_argument("--scene", choices=["box", "quadruped", "grammar"], default="box")
+    ap.add_argument("--scene", choices=list(SCENES), default="box")
     ap.add_argument("--values", type=int, nargs="*")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1)

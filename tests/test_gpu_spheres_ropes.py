@@ -1,0 +1,150 @@
+"""Sphere geometry and long chains on the GPU against the FP64 oracle,
+through the C ABI.
+
+Scenes: grammar robots whose modules are balls with probability 0.4
+(sphere/plane, sphere/box and sphere/sphere contacts), a cube with one ball
+(the BOX_AND_BALL-like scene), free balls on an incline (rolling closed form)
+and ropes of up to 25 links (the ARM_WITH_ROPE-like long chain).  Bars as in
+test_gpu_parity.py; for 25-link chains, whose mass matrices reach
+cond(M) ~ 1e5, the per-robot one-step bar is FP32's first-order solve bound
+cond(M) 2^-24, and passive ropes, chaotic even in flight, are held to the
+contact-rich bar (population-mean fitness within 2 %).
+"""
+import numpy as np
+import pytest
+
+from paper_2502_11129_b300 import population as P
+from paper_2502_11129_b300 import sim as S
+from tests.test_cpu_engine import _sphere_contact_kinds, rope_bar
+from tests.test_gpu_parity import MARGIN, _gpu_sim, _one_step, _report, ncores, oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def test_one_step_ball_modules():
+    pop = P.grammar(192, seed=81, ball_p=0.4)
+    q, v, s = P.random_state(pop, seed=82, angle=1.0)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(83).uniform(-0.05, 0.0, pop.n)
+    kinds = _sphere_contact_kinds(pop, q)
+    assert kinds.min() >= 10, kinds
+    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
+    near, bad, msg = _report("ball-modules", errs, margins)
+    assert not bad.any(), msg
+    assert near.mean() < 0.3, msg
+
+
+def test_one_step_box_and_ball():
+    pop = P.box_and_ball(128, seed=84)
+    q, v, s = P.random_state(pop, seed=85)
+    q[:, 2] = np.random.default_rng(86).uniform(0.03, 0.12, pop.n)
+    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
+    near, bad, msg = _report("box-and-ball", errs, margins)
+    assert not bad.any(), msg
+    assert near.mean() < 0.1, msg
+
+
+def test_sphere_contact_lists_match_oracle():
+    """Contact generation with balls: counts, bodies and order bit-exact,
+    geometry to 1e-5 (normals 1e-4)."""
+    O = oracle()
+    pop = P.grammar(96, seed=93, ball_p=0.5).as_float32()
+    q, v, s = P.random_state(pop, seed=94, angle=1.0)
+    q[:, 2] = pop.q0[:, 2] - 0.02
+    Q, V, Sx = S.state_rows(pop, q, v, s)
+    sm = _gpu_sim(pop)
+    sm.set_state(Q, V, Sx)
+    sm.step(1)
+    prm = O.default_params()
+    checked = with_sphere_pairs = 0
+    for i in range(pop.n):
+        m = O.model_from_population(pop, i)
+        c = O.contacts(m, Q[i, :O.nq(m)].astype(np.float64), prm)
+        if c["margin"] < MARGIN:
+            continue
+        g = sm.debug_contacts(i)
+        assert g["n"] == len(c["a"]), (i, g["n"], len(c["a"]))
+        assert np.array_equal(g["a"], c["a"]) and np.array_equal(g["b"], c["b"]), i
+        assert np.allclose(g["depth"], c["depth"], atol=1e-5), i
+        assert np.allclose(g["nrm"], c["n"], atol=1e-4), i
+        assert np.allclose(g["p"], c["p"] - Q[i, :3], atol=1e-5), i
+        checked += 1
+        with_sphere_pairs += any(b >= 0 and (m.geom[a] or m.geom[b]) for a, b in zip(c["a"], c["b"]))
+    assert checked > pop.n // 2 and with_sphere_pairs >= 5, (checked, with_sphere_pairs)
+
+
+@pytest.mark.parametrize("alpha_deg,mu,rolls", [(20.0, 0.5, True), (40.0, 0.1, False)])
+def test_ball_on_incline_on_gpu(alpha_deg, mu, rolls):
+    """Free balls on an incline (tilted gravity): rolling at (5/7) g sin(a)
+    with v = omega r when mu >= (2/7) tan(a), else sliding at
+    g (sin a - mu cos a); trajectories within 1e-4 m of the oracle."""
+    O = oracle()
+    G, a, r = 9.81, np.radians(alpha_deg), 0.05
+    grav = (G * np.sin(a), 0.0, -G * np.cos(a))
+    pop = P.boxes(16, seed=3).as_float32()
+    pop.geom[:, 0] = P.GEOM_SPHERE
+    pop.half[:, 0] = r
+    pop.mass[:, 0] = 0.5
+    q = np.zeros((16, 7))
+    q[:, 2] = r - 1e-4
+    q[:, 3] = 1.0
+    q[:, 0] = np.arange(16) * 0.3
+    Q, V, Sx = S.state_rows(pop, q, np.zeros((16, 6)), np.zeros((16, 64)))
+    sm = _gpu_sim(pop, mu=mu, gravity=grav)
+    sm.set_state(Q, V, Sx)
+    sm.step(100)
+    v0 = sm.read_state()[1].copy()
+    sm.step(400)
+    gq, gv, _, gst = sm.read_state()
+    assert (gst & 5).sum() == 0
+    acc = (gv[:, 0] - v0[:, 0]) / (400 * 0.002)
+    if rolls:
+        assert np.abs(acc - 5.0 / 7.0 * G * np.sin(a)).max() < 0.01 * G * np.sin(a)
+        assert np.abs(gv[:, 0] - gv[:, 4] * r).max() < 0.01 * np.abs(gv[:, 0]).min()
+    else:
+        assert np.abs(acc - G * (np.sin(a) - mu * np.cos(a))).max() < 0.01 * G * np.sin(a)
+    oq, _, _, _, _ = O.run_population(pop, Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64), 500,
+                                      prm=O.default_params(mu=mu, gravity=grav), threads=ncores())
+    assert np.abs(gq[:, :3] - oq[:, :3]).max() <= 1e-4
+
+
+def test_one_step_ropes_against_the_conditioning_bound():
+    for links, med in ((10, 1e-5), (25, 2e-4)):
+        pop = P.rope(48, seed=87, links=links)
+        q, v, s = P.random_state(pop, seed=88, angle=0.4)
+        q[:, 2] = pop.q0[:, 2] + np.random.default_rng(89).uniform(-0.04, 0.0, pop.n)
+        errs, margins, ost, gst, _ = _one_step(pop, q, v, s, actuate=0)
+        _report(f"rope-{links}", errs, margins)
+        rope_bar(pop, q, errs, margins < MARGIN, med)
+
+
+def test_ropes_contact_free_and_contact_rich():
+    """25-link ropes: lifted with the servos on, core within 1e-4 m of the
+    oracle over 200 steps; dropped passive ropes, population-mean fitness
+    within 2 % after 2000 steps."""
+    O = oracle()
+    pop = P.lift(P.rope(64, seed=91), 1.0).as_float32()
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+    sm = _gpu_sim(pop, box_box=0)
+    sm.set_state(Q, V, Sx)
+    prm = O.default_params(box_box=0)
+    oq, ov, os_ = Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64)
+    worst = 0.0
+    for _ in range(4):
+        sm.step(50)
+        oq, ov, os_, _, _ = O.run_population(pop, oq, ov, os_, 50, prm=prm, threads=ncores())
+        worst = max(worst, np.abs(sm.read_state()[0][:, :3] - oq[:, :3]).max())
+    sm.close()
+    assert worst <= 1e-4, worst
+    pop = P.rope(128, seed=92).as_float32()
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+    sm = _gpu_sim(pop, actuate=0)
+    sm.set_state(Q, V, Sx)
+    sm.step(2000)
+    gf, st = sm.fitness(), sm.read_state()[3]
+    sm.close()
+    oq, _, _, ost, _ = O.run_population(pop, pop.q0, pop.v0, P.cpg_initial(pop)[:, :2 * O.MAXB], 2000,
+                                        prm=O.default_params(actuate=0), threads=ncores())
+    of = O.fitness(pop.q0, oq)
+    print("rope mean fitness gpu %.6f oracle %.6f" % (gf.mean(), of.mean()))
+    assert (st & 5).sum() == 0 and (ost & 5).sum() == 0
+    assert abs(gf.mean() - of.mean()) <= 0.02 * of.mean()

@@ -16,6 +16,17 @@ def test_scene_sizes_and_tiling(monkeypatch):
     assert np.array_equal(g.nb[:64], base.nb[:64]) and np.array_equal(g.nb[64:128], base.nb[:64])
     with pytest.raises(ValueError):
         SW.scene("humanoid", 4)
+    bb = SW.scene("box_and_ball", 8, seed=2)
+    assert np.all(bb.nb == 2) and np.all(bb.geom[:, 1] == 1) and np.all(bb.geom[:, 0] == 0)
+    r = SW.scene("rope", 3)
+    assert np.all(r.nb == 26) and SW.SCENE_CFG["rope"] == dict(actuate=0)
+    gb = SW.scene("grammar_balls", 40)
+    assert (gb.geom == 1).any()
+    # a ball is always a leaf
+    for i in range(gb.n):
+        for b in range(1, int(gb.nb[i])):
+            if gb.geom[i, b] == 1:
+                assert not (gb.parent[i, :gb.nb[i]] == b).any()
 
 
 def test_t_quantile_and_table():
@@ -32,3 +43,6 @@ def test_tiny_sweeps_run_on_the_gpu():
     assert all(r["mean_s"] > 0 and len(r["seconds"]) == 2 for r in rows)
     rows = SW.sweep("steps", "grammar", values=[32, 64], reps=2, log=lambda *a: None)
     assert [r["steps"] for r in rows] == [32, 64]
+    for name in ("box_and_ball", "rope", "grammar_balls"):
+        rows = SW.sweep("variants", name, values=[32], reps=2, log=lambda *a: None)
+        assert rows[0]["mean_s"] > 0

@@ -22,7 +22,7 @@ from paper_2502_11129_b300 import sim as S
 
 pytestmark = pytest.mark.gpu
 
-NF, NI = 25, 5
+NF, NI = 26, 5
 TOL = 1e-6
 
 
@@ -57,13 +57,18 @@ def pack(pop):
             mf[i, 15:18, b] = p32.com[i, b]
             m = float(p32.mass[i, b])
             hx, hy, hz = (float(x) for x in p32.half[i, b])
+            sphere = int(p32.geom[i, b]) == P.GEOM_SPHERE
             mf[i, 18, b] = p32.mass[i, b]
-            mf[i, 19, b] = np.float32(m * (hy * hy + hz * hz) / 3.0)
-            mf[i, 20, b] = np.float32(m * (hx * hx + hz * hz) / 3.0)
-            mf[i, 21, b] = np.float32(m * (hx * hx + hy * hy) / 3.0)
+            if sphere:
+                mf[i, 19:22, b] = np.float32(0.4 * m * hx * hx)
+            else:
+                mf[i, 19, b] = np.float32(m * (hy * hy + hz * hz) / 3.0)
+                mf[i, 20, b] = np.float32(m * (hx * hx + hz * hz) / 3.0)
+                mf[i, 21, b] = np.float32(m * (hx * hx + hy * hy) / 3.0)
             mf[i, 22, b] = p32.w_int[i, b]
             mf[i, 23, b] = p32.w_cpl[i, b]
-            mf[i, 24, b] = np.float32(np.sqrt(hx * hx + hy * hy + hz * hz))
+            mf[i, 24, b] = np.float32(hx) if sphere else np.float32(np.sqrt(hx * hx + hy * hy + hz * hz))
+            mf[i, 25, b] = 1.0 if sphere else 0.0
             mi[i, 0, b] = -1 if b == 0 else parent[b]
             mi[i, 1, b] = int(p32.axis[i, b])
             mi[i, 2, b] = np.int32(path[b].view(np.int32))
@@ -102,7 +107,7 @@ def rel_err(a, b):
 def test_noalloc_matches_context_entry_on_two_calls():
     import torch
 
-    pop = P.grammar(48, seed=17).as_float32()
+    pop = P.grammar(48, seed=17, ball_p=0.25).as_float32()  # geometry field too
     q, v, s = P.random_state(pop, seed=3, angle=0.4)
     q[:, 2] = pop.q0[:, 2] - 0.004
     Q, V, Sx = S.state_rows(pop, q, v, s)
