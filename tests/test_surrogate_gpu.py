@@ -56,6 +56,25 @@ def test_forward_matches_oracle():
     s.close()
 
 
+def test_forward_tile_edges():
+    """The forward layers run in tiles of 128 rows: one row, a tile minus
+    one, one tile, one tile plus one and a ragged multi-tile batch, each
+    against the oracle."""
+    M = oracle()
+    rng = np.random.default_rng(3)
+    p = ref_params(4)
+    s = SG.Surrogate()
+    s.set_params(SG.pack_params(p))
+    for n in (1, 127, 128, 129, 300):
+        X = (rng.normal(size=(n, 128)) * 0.5).astype(np.float32)
+        y = s.predict(X)
+        yr, _ = M.forward(p, X)
+        scale = np.sqrt(np.mean(yr ** 2))
+        err = np.abs(y - yr) / np.maximum(np.abs(yr), scale)
+        assert err.max() <= 1e-2, (n, err.max())
+    s.close()
+
+
 def test_gradients_match_oracle():
     M = oracle()
     rng = np.random.default_rng(3)
