@@ -1,14 +1,17 @@
 // b3sur.cu -- learned fitness surrogate: BF16 MLP 128 -> 256 -> 256 -> 1 on
-// tensor cores (mma.sync m16n8k16, FP32 accumulate), Adam on FP32 master
-// weights, GPU genotype encoding and top-k selection.
+// tensor cores (forward layers: tcgen05.mma with the accumulator in tensor
+// memory; backward GEMMs with strided operands: mma.sync m16n8k16; FP32
+// accumulation throughout), Adam on FP32 master weights, GPU genotype
+// encoding and top-k selection.
 //
-// Dense layers run through one strided GEMM kernel C(m, n) = sum_k A(m, k)
-// B(n, k) whose epilogue is fused with the layer's bias + ReLU (forward) or
-// the ReLU mask (backward); the same kernel computes the weight gradients by
-// reducing over the batch (strided operands instead of transposed copies).
-// Weights and inputs are BF16; activations and backward operands are carried
-// as BF16 pairs (value = hi + lo, both BF16) and the GEMMs run over both
-// parts, so only the weights and inputs are rounded to 8 mantissa bits.
+// The forward layers (row-major operands, 128-row tiles, N = 256) run on
+// gemm_umma, whose epilogue is fused with the layer's bias + ReLU.  The
+// backward GEMMs run on gemm_bf16, a strided kernel C(m, n) = sum_k A(m, k)
+// B(n, k) that also computes the weight gradients by reducing over the batch
+// (strided operands instead of transposed copies).  Weights and inputs are
+// BF16; activations and backward operands are carried as BF16 pairs (value =
+// hi + lo, both BF16) and the GEMMs run over both parts, so only the weights
+// and inputs are rounded to 8 mantissa bits.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -36,8 +39,10 @@ constexpr int OB2 = OW2 + HID * HID;
 constexpr int OW3 = OB2 + HID;
 constexpr int OB3 = OW3 + HID;
 
-enum Epi { EPI_F32 = 0, EPI_BIAS_RELU_BF16 = 1, EPI_MASK_BF16_F32 = 2, EPI_F32_ADD = 3 };
+// epilogues: store FP32, add to FP32, or bias + ReLU + BF16 (hi, lo) split
+enum Epi { EPI_F32 = 0, EPI_F32_ADD = 1, EPI_BIAS_RELU_BF16 = 2 };
 
+// strided GEMM of the backward pass (EPI_F32 or EPI_F32_ADD)
 struct GemmArgs {
   int M, N, K;
   const bf16* A;
@@ -45,12 +50,7 @@ struct GemmArgs {
   const bf16* B;
   long lbn, lbk;  // B(n, k) = B[n * lbn + k * lbk]
   float* Cf;
-  bf16* Cb;
-  bf16* Cb_lo;  // EPI_MASK_BF16_F32: remainder v - bf16(v) as BF16
   long ldc;
-  const float* bias;
-  const bf16* mask;  // multiply by (mask(m, n) > 0)
-  long ldmask;
   int epi;
 };
 
@@ -125,26 +125,172 @@ __global__ void __launch_bounds__(128) gemm_bf16(GemmArgs g) {
         const int row = m0 + wm + mi * 16 + gid + 8 * (i >> 1);
         const int col = n0 + wn + ni * 8 + tig * 2 + (i & 1);
         if (row >= g.M || col >= g.N) continue;
-        float v = acc[mi][ni][i];
+        const float v = acc[mi][ni][i];
         const long o = (long)row * g.ldc + col;
-        if (g.epi == EPI_F32) {
-          g.Cf[o] = v;
-        } else if (g.epi == EPI_F32_ADD) {
-          g.Cf[o] += v;
-        } else if (g.epi == EPI_BIAS_RELU_BF16) {
-          v = fmaxf(v + g.bias[col], 0.f);
-          const bf16 hi = __float2bfloat16(v);
-          g.Cb[o] = hi;
-          g.Cb_lo[o] = __float2bfloat16(v - __bfloat162float(hi));
-        } else {
-          const bool on = __bfloat162float(g.mask[(long)row * g.ldmask + col]) > 0.f;
-          v = on ? v : 0.f;
-          const bf16 hi = __float2bfloat16(v);
-          g.Cb[o] = hi;
-          g.Cb_lo[o] = __float2bfloat16(v - __bfloat162float(hi));
-          g.Cf[o] = v;
-        }
+        if (g.epi == EPI_F32_ADD) g.Cf[o] += v;
+        else g.Cf[o] = v;
       }
+}
+
+// ---------------------------------------------------------------------------
+// Forward dense layers on the tcgen05 tensor cores.
+//
+// C(m, n) = sum over parts p of sum_k A_p(m, k) W(n, k) for a tile of 128 rows
+// and all HID = 256 outputs per CTA.  K is staged in chunks of 64 into shared
+// memory in the no-swizzle K-major core-matrix layout (a core matrix is 8 rows
+// x 16 bytes; the 8 core matrices of one 8-row group across a 64-wide chunk lie
+// 128 B apart, row groups 1 KB apart); one thread issues tcgen05.mma (M 128,
+// N 256, K 16; BF16 operands, FP32 accumulator in tensor memory) and commits
+// to an mbarrier that every thread waits on, with an iteration limit, before
+// the chunk's shared memory is refilled.  The epilogue reads the accumulator
+// with tcgen05.ld (thread = row, 16 columns at a time) and applies bias + ReLU
+// + the BF16 (hi, lo) split, or stores FP32.
+constexpr int UM_M = 128, UM_N = HID, UM_KC = 64;
+constexpr int UM_A_BYTES = UM_M * UM_KC * 2;  // 16 KB
+constexpr int UM_B_BYTES = UM_N * UM_KC * 2;  // 32 KB
+// requested dynamic shared memory: at most two CTAs per SM, so their 2 x 256
+// tensor-memory columns always fit the SM's 512 and an allocation never waits
+constexpr int UM_SMEM = 100 * 1024;
+constexpr unsigned UM_SPIN = 1u << 22;
+static_assert(UM_A_BYTES + UM_B_BYTES <= UM_SMEM, "one K chunk of both operands fits the shared memory");
+// kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A (bit 7)
+// and B (bit 10), both K-major, N / 8 at bit 17, M / 16 at bit 24
+constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_N >> 3) << 17) |
+                              ((uint32_t)(UM_M >> 4) << 24);
+
+struct UmmaArgs {
+  int M, K, parts;   // K a multiple of UM_KC
+  const bf16* A[2];  // parts, each M x K row-major
+  const bf16* W;     // UM_N x K row-major
+  const float* bias; // EPI_BIAS_RELU_BF16
+  float* Cf;         // EPI_F32 output, row stride UM_N
+  bf16* Cb;          // EPI_BIAS_RELU_BF16 outputs (hi, lo), row stride UM_N
+  bf16* Cb_lo;
+  int epi;
+  int* err;          // set to 1 when a wait gives up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading byte offset (K-adjacent
+// core matrices, 128 B), stride byte offset (8-row groups, 1 KB), version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (unsigned it = 0; it < UM_SPIN && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+  return done != 0;
+}
+
+__global__ void __launch_bounds__(128) gemm_umma(UmmaArgs g) {
+  extern __shared__ __align__(1024) unsigned char um_smem[];
+  unsigned char* As = um_smem;
+  unsigned char* Bs = um_smem + UM_A_BYTES;
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t mbar;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * UM_M;
+  const uint32_t bar = smem_u32(&mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(UM_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  uint32_t parity = 0;
+  bool ok = true;
+  const int nk = g.K / UM_KC;
+  for (int p = 0; p < g.parts && ok; ++p) {
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int k0 = kc * UM_KC;
+      // one 16-byte piece = 8 BF16 along K = one row of a core matrix
+      for (int e = tid; e < UM_M * 8; e += 128) {
+        const int r = e >> 3, j = e & 7, m = m0 + r;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (m < g.M) v = *reinterpret_cast<const uint4*>(g.A[p] + (size_t)m * g.K + k0 + 8 * j);
+        *reinterpret_cast<uint4*>(As + (r & 7) * 16 + j * 128 + (r >> 3) * 1024) = v;
+      }
+      for (int e = tid; e < UM_N * 8; e += 128) {
+        const int r = e >> 3, j = e & 7;
+        const uint4 v = *reinterpret_cast<const uint4*>(g.W + (size_t)r * g.K + k0 + 8 * j);
+        *reinterpret_cast<uint4*>(Bs + (r & 7) * 16 + j * 128 + (r >> 3) * 1024) = v;
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+#pragma unroll
+        for (int ks = 0; ks < UM_KC / 16; ++ks) {
+          const uint32_t acc = (p | kc | ks) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(tmem),
+              "l"(umma_desc(smem_u32(As) + ks * 256)), "l"(umma_desc(smem_u32(Bs) + ks * 256)), "r"(UM_IDESC),
+              "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+      }
+      ok = __syncthreads_and(mbar_wait(bar, parity) ? 1 : 0) != 0;
+      parity ^= 1u;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!ok) {
+    if (tid == 0) atomicExch(g.err, 1);
+  } else {
+    const int row = m0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < UM_N; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (row >= g.M) continue;
+      if (g.epi == EPI_F32) {
+        float4* o = reinterpret_cast<float4*>(g.Cf + (size_t)row * UM_N + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                             __uint_as_float(v[4 * q + 3]));
+      } else {
+        __align__(16) bf16 hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float x = fmaxf(__uint_as_float(v[j]) + g.bias[c0 + j], 0.f);
+          hi[j] = __float2bfloat16(x);
+          lo[j] = __float2bfloat16(x - __bfloat162float(hi[j]));
+        }
+        uint4* oh = reinterpret_cast<uint4*>(g.Cb + (size_t)row * UM_N + c0);
+        uint4* ol = reinterpret_cast<uint4*>(g.Cb_lo + (size_t)row * UM_N + c0);
+        oh[0] = reinterpret_cast<const uint4*>(hi)[0];
+        oh[1] = reinterpret_cast<const uint4*>(hi)[1];
+        ol[0] = reinterpret_cast<const uint4*>(lo)[0];
+        ol[1] = reinterpret_cast<const uint4*>(lo)[1];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_N));
 }
 
 // h = relu(z + b) as FP32 and as a BF16 pair (hi, lo)
@@ -452,6 +598,7 @@ struct sur_ctx {
   float* scores = nullptr;
   int* idx = nullptr;
   size_t cap_scores = 0;
+  int* uerr = nullptr;     // set by gemm_umma when a tensor-core wait gives up
 };
 
 namespace {
@@ -491,22 +638,23 @@ cudaError_t refresh_bf16(sur_ctx* c) {
 // carried as BF16 pairs (hi + lo) and each GEMM consuming them runs on both
 // parts, so the forward pass rounds only the weights and inputs to BF16.
 cudaError_t forward_batch(sur_ctx* c, int n) {
-  GemmArgs g{};
-  g.M = n; g.N = HID; g.K = IN;
-  g.A = c->xb; g.lam = IN; g.lak = 1;
-  g.B = c->w1b; g.lbn = IN; g.lbk = 1;
-  g.Cb = c->h1; g.Cb_lo = c->h1lo; g.ldc = HID; g.bias = c->p + OB1; g.epi = EPI_BIAS_RELU_BF16;
-  cudaError_t e = launch_gemm(c->stream, g);
+  // layer 1: H1 = relu(X W1^T + b1) as a BF16 pair; layer 2: Z2 = (H1 + H1lo) W2^T
+  // with both parts accumulated in one tensor-memory accumulator
+  const int grid = (n + UM_M - 1) / UM_M;
+  UmmaArgs g{};
+  g.M = n; g.K = IN; g.parts = 1;
+  g.A[0] = c->xb; g.W = c->w1b; g.bias = c->p + OB1;
+  g.Cb = c->h1; g.Cb_lo = c->h1lo; g.epi = EPI_BIAS_RELU_BF16; g.err = c->uerr;
+  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(g);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  for (int part = 0; part < 2; ++part) {
-    GemmArgs h{};
-    h.M = n; h.N = HID; h.K = HID;
-    h.A = part ? c->h1lo : c->h1; h.lam = HID; h.lak = 1;
-    h.B = c->w2b; h.lbn = HID; h.lbk = 1;
-    h.Cf = c->z2f; h.ldc = HID; h.epi = part ? EPI_F32_ADD : EPI_F32;
-    e = launch_gemm(c->stream, h);
-    if (e != cudaSuccess) return e;
-  }
+  UmmaArgs h{};
+  h.M = n; h.K = HID; h.parts = 2;
+  h.A[0] = c->h1; h.A[1] = c->h1lo; h.W = c->w2b;
+  h.Cf = c->z2f; h.epi = EPI_F32; h.err = c->uerr;
+  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(h);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   bias_relu_split<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->z2f, c->p + OB2, n, c->h2f, c->h2,
                                                                            c->h2lo);
   out_layer<<<(n + 7) / 8, 256, 0, c->stream>>>(c->h2f, c->w3b, c->p + OB3, n, c->y);
@@ -596,9 +744,17 @@ int ensure_scores(sur_ctx* ctx, size_t n) {
 void free_all(sur_ctx* c) {
   void* ptrs[] = {c->p, c->g, c->m, c->v, c->w1b, c->w2b, c->w3b, c->xb, c->h1, c->h2, c->dz2, c->dz1,
                   c->dz2lo, c->dz1lo, c->h1lo, c->h2lo, c->h2f, c->z2f, c->dz1f, c->y, c->dy, c->tb, c->part, c->xfull, c->tfull, c->perm, c->topk_work, c->scores,
-                  c->idx};
+                  c->idx, c->uerr};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+}
+
+// after a stream synchronisation: did a tensor-core wait give up?
+int check_umma(sur_ctx* ctx) {
+  int h = 0;
+  CK(cudaMemcpy(&h, ctx->uerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) return fail(ctx, SUR_ECUDA, "gemm_umma: a tensor-core completion wait gave up");
+  return SUR_OK;
 }
 
 int read_loss(sur_ctx* ctx, int n, float* loss_out) {
@@ -606,6 +762,7 @@ int read_loss(sur_ctx* ctx, int n, float* loss_out) {
   std::vector<float> part(nblk);
   CK(cudaMemcpyAsync(part.data(), ctx->part, nblk * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (int rc = check_umma(ctx)) return rc;
   double s = 0.0;
   for (float x : part) s += x;
   if (loss_out) *loss_out = (float)(s / n);
@@ -671,7 +828,9 @@ int sur_create(const sur_config* cfg, sur_ctx_t** out) {
             dalloc(&ctx->dz1f, B * HID) == cudaSuccess && dalloc(&ctx->y, B) == cudaSuccess &&
             dalloc(&ctx->dy, B) == cudaSuccess && dalloc(&ctx->tb, B) == cudaSuccess &&
             dalloc(&ctx->part, (B + 255) / 256) == cudaSuccess &&
-            dalloc(&ctx->topk_work, (size_t)2 * SUR_MAX_TOPK) == cudaSuccess;
+            dalloc(&ctx->topk_work, (size_t)2 * SUR_MAX_TOPK) == cudaSuccess && dalloc(&ctx->uerr, 1) == cudaSuccess &&
+            cudaMemset(ctx->uerr, 0, sizeof(int)) == cudaSuccess &&
+            cudaFuncSetAttribute(gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess;
   if (!ok) {
     free_all(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -777,6 +936,7 @@ int sur_predict(sur_ctx_t* ctx, const float* X, int32_t n, float* y_out) {
     CK(forward_batch(ctx, nb));
     CK(cudaMemcpyAsync(tmp.data(), ctx->y, nb * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (int rc2 = check_umma(ctx)) return rc2;
     for (int i = 0; i < nb; ++i) y_out[b0 + i] = (float)(ctx->mu + ctx->sigma * (double)tmp[i]);
   }
   return SUR_OK;
