@@ -36,7 +36,7 @@ typedef struct sur_ctx sur_ctx_t;
 
 #define SUR_IN_DIM 128
 #define SUR_HIDDEN 256
-#define SUR_MAX_BATCH 8192
+#define SUR_MAX_BATCH 65536
 #define SUR_MAX_TOPK 8192
 
 typedef enum { SUR_OK = 0, SUR_EINVAL = -1, SUR_ECUDA = -2, SUR_ENOMEM = -3 } sur_status;

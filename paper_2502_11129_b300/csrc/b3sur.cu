@@ -5,13 +5,16 @@
 // encoding and top-k selection.
 //
 // The forward layers (row-major operands, 128-row tiles, N = 256) run on
-// gemm_umma, whose epilogue is fused with the layer's bias + ReLU.  The
+// gemm_umma (TMA + tcgen05), whose epilogue is fused with the layer's bias +
+// ReLU.  The
 // backward GEMMs run on gemm_bf16, a strided kernel C(m, n) = sum_k A(m, k)
 // B(n, k) that also computes the weight gradients by reducing over the batch
 // (strided operands instead of transposed copies).  Weights and inputs are
 // BF16; activations and backward operands are carried as BF16 pairs (value =
 // hi + lo, both BF16) and the GEMMs run over both parts, so only the weights
 // and inputs are rounded to 8 mantissa bits.
+#include <cuda.h>  // CUtensorMap and its enums (the driver entry point is fetched at run time)
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -133,35 +136,40 @@ __global__ void __launch_bounds__(128) gemm_bf16(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward dense layers on the tcgen05 tensor cores.
+// Forward dense layers on the tcgen05 tensor cores, fed by TMA.
 //
 // C(m, n) = sum over parts p of sum_k A_p(m, k) W(n, k) for a tile of 128 rows
-// and all HID = 256 outputs per CTA.  K is staged in chunks of 64 into shared
-// memory in the no-swizzle K-major core-matrix layout (a core matrix is 8 rows
-// x 16 bytes; the 8 core matrices of one 8-row group across a 64-wide chunk lie
-// 128 B apart, row groups 1 KB apart); one thread issues tcgen05.mma (M 128,
-// N 256, K 16; BF16 operands, FP32 accumulator in tensor memory) and commits
-// to an mbarrier that every thread waits on, with an iteration limit, before
-// the chunk's shared memory is refilled.  The epilogue reads the accumulator
-// with tcgen05.ld (thread = row, 16 columns at a time) and applies bias + ReLU
-// + the BF16 (hi, lo) split, or stores FP32.
-constexpr int UM_M = 128, UM_N = HID, UM_KC = 64;
-constexpr int UM_A_BYTES = UM_M * UM_KC * 2;  // 16 KB
-constexpr int UM_B_BYTES = UM_N * UM_KC * 2;  // 32 KB
+// and all HID = 256 outputs per CTA.  K runs in chunks of 64 through a
+// two-stage shared-memory ring.  One thread produces and issues: per chunk it
+// arms the stage's `full` mbarrier with the chunk's byte count and starts 16
+// tensor copies (cp.async.bulk.tensor.2d), each an 8-element K slice of 128 A
+// rows (2 KB) or 256 W rows (4 KB); a box of 8 BF16 x rows lands as rows x 16 B,
+// which is the no-swizzle K-major core-matrix layout with 8-row groups 128 B
+// apart and K-adjacent core matrices one slice apart.  Once a stage is full it
+// issues the chunk's four tcgen05.mma (M 128, N 256, K 16; BF16 operands, FP32
+// accumulator in tensor memory) and commits them to the stage's `empty`
+// mbarrier, then refills the stage the previous chunk used as soon as that
+// chunk's MMAs have drained it, so copies overlap the tensor core.  A last
+// commit to the `done` mbarrier releases the epilogue: tcgen05.ld (thread =
+// row, 16 columns at a time) with bias + ReLU + the BF16 (hi, lo) split, or an
+// FP32 store.  Every wait has an iteration limit; a give-up sets a device flag
+// that the host checks after its next synchronisation.
+constexpr int UM_M = 128, UM_N = HID, UM_KC = 64, UM_STAGES = 2;
+constexpr int UM_A_SLICE = UM_M * 16, UM_B_SLICE = UM_N * 16;            // bytes per 8-wide K slice
+constexpr int UM_A_STAGE = UM_A_SLICE * (UM_KC / 8), UM_B_STAGE = UM_B_SLICE * (UM_KC / 8);
+constexpr int UM_STAGE = UM_A_STAGE + UM_B_STAGE;                          // 48 KB
 // requested dynamic shared memory: at most two CTAs per SM, so their 2 x 256
 // tensor-memory columns always fit the SM's 512 and an allocation never waits
 constexpr int UM_SMEM = 100 * 1024;
 constexpr unsigned UM_SPIN = 1u << 22;
-static_assert(UM_A_BYTES + UM_B_BYTES <= UM_SMEM, "one K chunk of both operands fits the shared memory");
+static_assert(UM_STAGES * UM_STAGE <= UM_SMEM, "the ring fits the shared memory");
 // kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A (bit 7)
 // and B (bit 10), both K-major, N / 8 at bit 17, M / 16 at bit 24
 constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_N >> 3) << 17) |
                               ((uint32_t)(UM_M >> 4) << 24);
 
 struct UmmaArgs {
-  int M, K, parts;   // K a multiple of UM_KC
-  const bf16* A[2];  // parts, each M x K row-major
-  const bf16* W;     // UM_N x K row-major
+  int M, K, parts;   // K a multiple of UM_KC; parts 1 or 2 (A maps 0 and 1)
   const float* bias; // EPI_BIAS_RELU_BF16
   float* Cf;         // EPI_F32 output, row stride UM_N
   bf16* Cb;          // EPI_BIAS_RELU_BF16 outputs (hi, lo), row stride UM_N
@@ -172,10 +180,11 @@ struct UmmaArgs {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start address, leading byte offset (K-adjacent
-// core matrices, 128 B), stride byte offset (8-row groups, 1 KB), version 1, no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+// shared-memory matrix descriptor: start address, leading byte offset (between
+// K-adjacent core matrices: one slice), stride byte offset (between 8-row
+// groups: 128 B), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t slice_bytes) {
+  return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)(slice_bytes >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
          ((uint64_t)1 << 46);
 }
 
@@ -185,70 +194,98 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity));
+        : "r"(bar), "r"(parity)
+        : "memory");
   return done != 0;
 }
 
-__global__ void __launch_bounds__(128) gemm_umma(UmmaArgs g) {
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtensorMap mA0,
+                                                 const __grid_constant__ CUtensorMap mA1,
+                                                 const __grid_constant__ CUtensorMap mW, UmmaArgs g) {
   extern __shared__ __align__(1024) unsigned char um_smem[];
-  unsigned char* As = um_smem;
-  unsigned char* Bs = um_smem + UM_A_BYTES;
   __shared__ uint32_t tmem_slot;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int failed;
+  __shared__ __align__(8) uint64_t full_bar[UM_STAGES], empty_bar[UM_STAGES], done_bar;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * UM_M;
-  const uint32_t bar = smem_u32(&mbar);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(UM_N));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    for (int s = 0; s < UM_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    failed = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  uint32_t parity = 0;
-  bool ok = true;
-  const int nk = g.K / UM_KC;
-  for (int p = 0; p < g.parts && ok; ++p) {
-    for (int kc = 0; kc < nk && ok; ++kc) {
-      const int k0 = kc * UM_KC;
-      // one 16-byte piece = 8 BF16 along K = one row of a core matrix
-      for (int e = tid; e < UM_M * 8; e += 128) {
-        const int r = e >> 3, j = e & 7, m = m0 + r;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (m < g.M) v = *reinterpret_cast<const uint4*>(g.A[p] + (size_t)m * g.K + k0 + 8 * j);
-        *reinterpret_cast<uint4*>(As + (r & 7) * 16 + j * 128 + (r >> 3) * 1024) = v;
+  const int nk = g.K / UM_KC, nchunks = g.parts * nk;
+  if (tid == 0) {
+    const uint32_t ring = smem_u32(um_smem);
+    auto load = [&](int c) {
+      const int s = c % UM_STAGES, k0 = (c % nk) * UM_KC;
+      const CUtensorMap* ma = (c / nk) ? &mA1 : &mA0;
+      const uint32_t a = ring + s * UM_STAGE, b = a + UM_A_STAGE, bar = smem_u32(&full_bar[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(UM_STAGE) : "memory");
+      for (int j = 0; j < UM_KC / 8; ++j) {
+        tma_2d(a + j * UM_A_SLICE, ma, k0 + 8 * j, m0, bar);
+        tma_2d(b + j * UM_B_SLICE, &mW, k0 + 8 * j, 0, bar);
       }
-      for (int e = tid; e < UM_N * 8; e += 128) {
-        const int r = e >> 3, j = e & 7;
-        const uint4 v = *reinterpret_cast<const uint4*>(g.W + (size_t)r * g.K + k0 + 8 * j);
-        *reinterpret_cast<uint4*>(Bs + (r & 7) * 16 + j * 128 + (r >> 3) * 1024) = v;
-      }
-      asm volatile("fence.proxy.async.shared::cta;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
+    };
+    bool ok = true;
+    load(0);
+    if (nchunks > 1) load(1);
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s = c % UM_STAGES;
+      ok = mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((c / UM_STAGES) & 1));
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
+      const uint32_t a = ring + s * UM_STAGE, b = a + UM_A_STAGE;
 #pragma unroll
-        for (int ks = 0; ks < UM_KC / 16; ++ks) {
-          const uint32_t acc = (p | kc | ks) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(tmem),
-              "l"(umma_desc(smem_u32(As) + ks * 256)), "l"(umma_desc(smem_u32(Bs) + ks * 256)), "r"(UM_IDESC),
-              "r"(acc));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+      for (int ks = 0; ks < UM_KC / 16; ++ks) {
+        const uint32_t acc = (c | ks) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(tmem),
+            "l"(umma_desc(a + 2 * ks * UM_A_SLICE, UM_A_SLICE)), "l"(umma_desc(b + 2 * ks * UM_B_SLICE, UM_B_SLICE)),
+            "r"(UM_IDESC), "r"(acc));
       }
-      ok = __syncthreads_and(mbar_wait(bar, parity) ? 1 : 0) != 0;
-      parity ^= 1u;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty_bar[s]))
+                   : "memory");
+      // refill the stage the previous chunk used once its MMAs have read it
+      if (c >= 1 && c + 1 < nchunks) {
+        const int sp = (c - 1) % UM_STAGES;
+        ok = mbar_wait(smem_u32(&empty_bar[sp]), (uint32_t)(((c - 1) / UM_STAGES) & 1));
+        if (ok) load(c + 1);
+      }
+    }
+    if (ok) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&done_bar))
+                   : "memory");
+    } else {
+      failed = 1;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&done_bar)) : "memory");
     }
   }
+  const bool done = mbar_wait(smem_u32(&done_bar), 0u);
+  const bool ok = __syncthreads_and(done && !failed) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok) {
     if (tid == 0) atomicExch(g.err, 1);
@@ -599,6 +636,7 @@ struct sur_ctx {
   int* idx = nullptr;
   size_t cap_scores = 0;
   int* uerr = nullptr;     // set by gemm_umma when a tensor-core wait gives up
+  CUtensorMap tm_x{}, tm_h1{}, tm_h1lo{}, tm_w1{}, tm_w2{};  // TMA maps of the forward operands
 };
 
 namespace {
@@ -643,16 +681,14 @@ cudaError_t forward_batch(sur_ctx* c, int n) {
   const int grid = (n + UM_M - 1) / UM_M;
   UmmaArgs g{};
   g.M = n; g.K = IN; g.parts = 1;
-  g.A[0] = c->xb; g.W = c->w1b; g.bias = c->p + OB1;
-  g.Cb = c->h1; g.Cb_lo = c->h1lo; g.epi = EPI_BIAS_RELU_BF16; g.err = c->uerr;
-  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(g);
+  g.bias = c->p + OB1; g.Cb = c->h1; g.Cb_lo = c->h1lo; g.epi = EPI_BIAS_RELU_BF16; g.err = c->uerr;
+  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(c->tm_x, c->tm_x, c->tm_w1, g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   UmmaArgs h{};
   h.M = n; h.K = HID; h.parts = 2;
-  h.A[0] = c->h1; h.A[1] = c->h1lo; h.W = c->w2b;
   h.Cf = c->z2f; h.epi = EPI_F32; h.err = c->uerr;
-  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(h);
+  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(c->tm_h1, c->tm_h1lo, c->tm_w2, h);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bias_relu_split<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->z2f, c->p + OB2, n, c->h2f, c->h2,
@@ -787,6 +823,31 @@ int stage_batch(sur_ctx* ctx, const float* X, const float* t, int n) {
 
 }  // namespace
 
+namespace {
+
+// TMA map of a row-major BF16 matrix (rows x cols) read in boxes of 8 columns
+// x box_rows rows; cuTensorMapEncodeTiled is taken from the driver at run time
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * sizeof(bf16)};
+  const cuuint32_t box[2] = {8, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 extern "C" {
 
 int sur_create(const sur_config* cfg, sur_ctx_t** out) {
@@ -830,7 +891,10 @@ int sur_create(const sur_config* cfg, sur_ctx_t** out) {
             dalloc(&ctx->part, (B + 255) / 256) == cudaSuccess &&
             dalloc(&ctx->topk_work, (size_t)2 * SUR_MAX_TOPK) == cudaSuccess && dalloc(&ctx->uerr, 1) == cudaSuccess &&
             cudaMemset(ctx->uerr, 0, sizeof(int)) == cudaSuccess &&
-            cudaFuncSetAttribute(gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess;
+            cudaFuncSetAttribute(gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
+            make_map(&ctx->tm_x, ctx->xb, B, IN, UM_M) && make_map(&ctx->tm_h1, ctx->h1, B, HID, UM_M) &&
+            make_map(&ctx->tm_h1lo, ctx->h1lo, B, HID, UM_M) && make_map(&ctx->tm_w1, ctx->w1b, HID, IN, UM_N) &&
+            make_map(&ctx->tm_w2, ctx->w2b, HID, HID, UM_N);
   if (!ok) {
     free_all(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

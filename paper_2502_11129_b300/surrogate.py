@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libb3sur.so")
 IN_DIM, HIDDEN = 128, 256
 NPARAMS = HIDDEN * IN_DIM + HIDDEN + HIDDEN * HIDDEN + HIDDEN + HIDDEN + 1
-MAX_BATCH, MAX_TOPK = 8192, 8192
+MAX_BATCH, MAX_TOPK = 65536, 8192
 EXPORTS = ["sur_create", "sur_destroy", "sur_encode", "sur_train", "sur_predict", "sur_topk",
            "sur_gradients", "sur_train_step", "sur_get_params", "sur_set_params", "sur_last_error"]
 STATUS = {0: "SUR_OK", -1: "SUR_EINVAL", -2: "SUR_ECUDA", -3: "SUR_ENOMEM"}
