@@ -270,6 +270,7 @@ def run_ours(args, world, rank, local, dist):
                                   f"{args.chunk}-step graph replays",
                       "variants_per_gpu": args.variants, "sim_steps_per_bench_step": args.chunk,
                       "steps_per_launch": spl, "warps_per_block": shape["warps_per_block"],
+                      "warps_per_sm": shape["warps_per_sm"],
                       "l2": "flushed between timed steps (256 MiB write)",
                       "contacts_per_variant_step": contacts_per_vs, "frozen_variants": frozen,
                       "parallelism": f"dp{world} (independent robots per GPU)"},

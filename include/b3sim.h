@@ -104,6 +104,11 @@ typedef struct {
                                  distinct phases per SM at a time, but every
                                  phase waits for the block's slowest robot);
                                  0: off (default)                           */
+    int32_t warps_per_sm;     /* resident warps per SM the step kernel's
+                                 registers are sized for: 16 (128 registers a
+                                 thread) or 12 (168: each warp faster, fewer
+                                 robots at once; not with 8 warps per
+                                 block); 0: autotuned (default 16)          */
 } sim_config;
 
 /* Model of one variant.  Arrays have n_bodies entries (per body) unless
@@ -180,10 +185,12 @@ int sim_fitness(sim_ctx_t* ctx, float* out, int32_t n);
 int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps);
 
 /* The launch shape sim_step_n uses now (after sim_autotune, the chosen one):
- * warps per block, phase lock and steps per persistent launch.  Any output
- * may be NULL. */
+ * warps per block, phase lock, steps per persistent launch and the resident
+ * warps per SM the kernel's registers are sized for.  Any output may be
+ * NULL. */
 int sim_launch_shape(const sim_ctx_t* ctx, int32_t* warps_per_block, int32_t* phase_lock,
-                     int32_t* steps_per_launch);
+                     int32_t* steps_per_launch,
+                     int32_t* warps_per_sm);
 
 /* Work counters accumulated since sim_set_population (synchronises). */
 int sim_counters_read(sim_ctx_t* ctx, sim_counters* out);

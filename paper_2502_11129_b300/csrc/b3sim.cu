@@ -62,6 +62,7 @@ struct sim_ctx {
   int steps_per_launch = kDefaultStepsPerLaunch;
   int wpb = 4;
   bool lock = false;  // phase-locked launches (warps of a block in step)
+  int wpsm = 16;      // resident warps per SM the kernel's registers are sized for
   std::map<long long, cudaGraphExec_t> graphs;
 };
 
@@ -274,41 +275,55 @@ cudaError_t cost_order(const LaunchArgs& a) {
   return cudaGetLastError();
 }
 
-template <int WPB, bool LOCK>
+template <int WPB, bool LOCK, int WPSM>
 cudaError_t launch_wpb(const LaunchArgs& a, int nsteps) {
   const size_t sm = smem_bytes(WPB);
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e =
-        cudaFuncSetAttribute(b3::step_kernel<WPB, LOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(b3::step_kernel<WPB, LOCK, WPSM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   dim3 grid((a.n + WPB - 1) / WPB), block(32 * WPB);
-  b3::step_kernel<WPB, LOCK><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s, a.status,
-                                                           a.counters, a.scratch, a.lastnc, a.order, a.n, nsteps,
-                                                           a.P);
+  b3::step_kernel<WPB, LOCK, WPSM><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s,
+                                                                 a.status, a.counters, a.scratch, a.lastnc,
+                                                                 a.order, a.n, nsteps, a.P);
   return cudaGetLastError();
 }
 
-// phase locking needs a block of several warps; with one warp it is a no-op
-cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb, bool lock) {
+template <int WPSM>
+cudaError_t launch_shape(const LaunchArgs& a, int nsteps, int wpb, bool lock) {
+  // phase locking needs a block of several warps; with one warp it is a no-op
   switch (wpb) {
-    case 1: return launch_wpb<1, false>(a, nsteps);
-    case 2: return lock ? launch_wpb<2, true>(a, nsteps) : launch_wpb<2, false>(a, nsteps);
-    case 4: return lock ? launch_wpb<4, true>(a, nsteps) : launch_wpb<4, false>(a, nsteps);
-    case 8: return lock ? launch_wpb<8, true>(a, nsteps) : launch_wpb<8, false>(a, nsteps);
+    case 1: return launch_wpb<1, false, WPSM>(a, nsteps);
+    case 2: return lock ? launch_wpb<2, true, WPSM>(a, nsteps) : launch_wpb<2, false, WPSM>(a, nsteps);
+    case 4: return lock ? launch_wpb<4, true, WPSM>(a, nsteps) : launch_wpb<4, false, WPSM>(a, nsteps);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool lock, int spl) {
+// a launch shape: warps per block, phase lock, resident warps per SM (16 or
+// 12; blocks of 8 warps only with 16)
+bool shape_ok(int wpb, int wpsm) {
+  return (wpsm == 16 && (wpb == 1 || wpb == 2 || wpb == 4 || wpb == 8)) ||
+         (wpsm == 12 && (wpb == 1 || wpb == 2 || wpb == 4));
+}
+
+cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb, bool lock, int wpsm) {
+  if (!shape_ok(wpb, wpsm)) return cudaErrorInvalidValue;
+  if (wpsm == 12) return launch_shape<12>(a, nsteps, wpb, lock);
+  if (wpb == 8) return lock ? launch_wpb<8, true, 16>(a, nsteps) : launch_wpb<8, false, 16>(a, nsteps);
+  return launch_shape<16>(a, nsteps, wpb, lock);
+}
+
+cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool lock, int wpsm, int spl) {
   for (int done = 0; done < n_steps; done += spl) {
     if (a.order) {
       cudaError_t e = cost_order(a);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb, lock);
+    cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb, lock, wpsm);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -320,8 +335,8 @@ LaunchArgs ctx_args(sim_ctx* ctx) {
                     ctx->d_lastnc, ctx->d_order, ctx->d_order_hist, ctx->n, ctx->P, ctx->stream};
 }
 
-cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int spl) {
-  return enqueue_launches(ctx_args(ctx), n_steps, wpb, lock, spl);
+cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int wpsm, int spl) {
+  return enqueue_launches(ctx_args(ctx), n_steps, wpb, lock, wpsm, spl);
 }
 
 bool config_ok(const sim_config* cfg) {
@@ -330,7 +345,9 @@ bool config_ok(const sim_config* cfg) {
          cfg->mu >= 0.f && cfg->steps_per_launch >= 0 && cfg->max_correct_vel > 0.f && cfg->min_cfm >= 0.f &&
          (cfg->warps_per_block == 0 || cfg->warps_per_block == 1 || cfg->warps_per_block == 2 ||
           cfg->warps_per_block == 4 || cfg->warps_per_block == 8) &&
-         (cfg->phase_lock == 0 || cfg->phase_lock == 1);
+         (cfg->phase_lock == 0 || cfg->phase_lock == 1) &&
+         (cfg->warps_per_sm == 0 || cfg->warps_per_sm == 12 || cfg->warps_per_sm == 16) &&
+         !(cfg->warps_per_sm == 12 && cfg->warps_per_block == 8);
 }
 
 // FP32 step constants from a configuration (ERP / CFM of the soft contacts
@@ -473,8 +490,9 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
                     pop->q,       pop->v,       pop->cpg, pop->status, a.counters, a.scratch, a.lastnc,
                     nullptr,      nullptr,      pop->n,   make_params(cfg), stream};
     const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
+    const int wpsm = cfg->warps_per_sm > 0 ? cfg->warps_per_sm : 16;
     const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : kDefaultStepsPerLaunch;
-    e = enqueue_launches(args, n_steps, wpb, cfg->phase_lock == 1, spl);
+    e = enqueue_launches(args, n_steps, wpb, cfg->phase_lock == 1, wpsm, spl);
   }
   if (e != cudaSuccess) {
     g_create_error_buf = std::string("sim_step_n_noalloc: ") + cudaGetErrorString(e);
@@ -521,6 +539,7 @@ int sim_create(const sim_config* cfg, sim_ctx_t** out) {
   ctx->P = make_params(cfg);
   if (cfg->steps_per_launch > 0) ctx->steps_per_launch = cfg->steps_per_launch;
   if (cfg->warps_per_block > 0) ctx->wpb = cfg->warps_per_block;
+  if (cfg->warps_per_sm > 0) ctx->wpsm = cfg->warps_per_sm;
   ctx->lock = cfg->phase_lock == 1;
   *out = ctx;
   return SIM_OK;
@@ -631,12 +650,12 @@ int sim_step_n(sim_ctx_t* ctx, int32_t n_steps) {
   if (n_steps < 0) return fail(ctx, SIM_EINVAL, "sim_step_n: n_steps < 0");
   if (n_steps == 0) return SIM_OK;
   CK(cudaSetDevice(ctx->cfg.device));
-  const long long key = ((long long)n_steps << 8) | (ctx->lock ? 16 : 0) | ctx->wpb;
+  const long long key = ((long long)n_steps << 8) | (ctx->wpsm == 12 ? 32 : 0) | (ctx->lock ? 16 : 0) | ctx->wpb;
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = enqueue_steps(ctx, n_steps, ctx->wpb, ctx->lock, ctx->steps_per_launch);
+    cudaError_t le = enqueue_steps(ctx, n_steps, ctx->wpb, ctx->lock, ctx->wpsm, ctx->steps_per_launch);
     cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
     if (le != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -717,40 +736,49 @@ int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  // warps per block; the phase lock stays as configured: a short probe
-  // from one state does not show its cost in later steps, where the
-  // slowest robot of a block sets the pace of every phase boundary
+  // warps per block x resident warps per SM (unless configured); the phase
+  // lock stays as configured: a short probe from one state does not show
+  // its cost in later steps, where the slowest robot of a block sets the
+  // pace of every phase boundary
   const int cands[4] = {1, 2, 4, 8};
+  const int occs[2] = {16, 12};
   float best_ms = 1e30f;
-  int best = ctx->wpb;
-  for (const int c : cands) {
-    const bool lk = ctx->lock;
-    cudaError_t e = restore();
-    if (e != cudaSuccess) break;
-    e = enqueue_steps(ctx, probe_steps, c, lk, probe_steps);  // warm-up (and attribute set-up)
-    if (e != cudaSuccess) continue;
-    restore();
-    cudaEventRecord(e0, ctx->stream);
-    e = enqueue_steps(ctx, probe_steps, c, lk, probe_steps);
-    cudaEventRecord(e1, ctx->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess || e != cudaSuccess) continue;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+  int best = ctx->wpb, best_occ = ctx->wpsm;
+  for (const int occ : occs) {
+    if (ctx->cfg.warps_per_sm > 0 && occ != ctx->cfg.warps_per_sm) continue;
+    for (const int c : cands) {
+      if (!shape_ok(c, occ)) continue;
+      const bool lk = ctx->lock;
+      cudaError_t e = restore();
+      if (e != cudaSuccess) break;
+      e = enqueue_steps(ctx, probe_steps, c, lk, occ, probe_steps);  // warm-up (and attribute set-up)
+      if (e != cudaSuccess) continue;
+      restore();
+      cudaEventRecord(e0, ctx->stream);
+      e = enqueue_steps(ctx, probe_steps, c, lk, occ, probe_steps);
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess || e != cudaSuccess) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+        best_occ = occ;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(restore());
   ctx->wpb = best;
+  ctx->wpsm = best_occ;
   return SIM_OK;
 }
 
 int sim_launch_shape(const sim_ctx_t* ctx, int32_t* warps_per_block, int32_t* phase_lock,
-                     int32_t* steps_per_launch) {
+                     int32_t* steps_per_launch, int32_t* warps_per_sm) {
   if (!ctx) return SIM_EINVAL;
+  if (warps_per_sm) *warps_per_sm = ctx->wpsm;
   if (warps_per_block) *warps_per_block = ctx->wpb;
   if (phase_lock) *phase_lock = ctx->lock ? 1 : 0;
   if (steps_per_launch) *steps_per_launch = ctx->steps_per_launch;

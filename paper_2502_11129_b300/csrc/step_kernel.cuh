@@ -115,12 +115,13 @@ struct Counters {
   unsigned long long contacts, narrow, broad, steps, cycles;
 };
 
-// resident warps per SM the register budget is sized for (65536 / (32 x warps)
-// registers per thread)
-#ifndef B3_WARPS_PER_SM
-#define B3_WARPS_PER_SM 16
-#endif
-constexpr int kWarpsPerSM = B3_WARPS_PER_SM;
+// Resident warps per SM that a kernel instance's register budget is sized
+// for (WPSM): 16 (128 registers per thread) or 12 (168).  With 12 the compiler
+// keeps more values in registers and each warp runs its step faster, but
+// fewer robots run at once: the first wins where a launch lasts as long as
+// its slowest robot (a few thousand uneven robots), the second where the
+// SMs' throughput decides (tens of thousands of robots).  The autotuner
+// times both.
 
 // Block barriers per step of a phase-locked launch (LOCK): the warps of a
 // block pass every phase boundary together, so that the SM runs few distinct
@@ -128,8 +129,8 @@ constexpr int kWarpsPerSM = B3_WARPS_PER_SM;
 // block's slowest robot at each boundary.
 constexpr int kLockBarriers = 5;
 
-template <int WPB, bool LOCK>
-__global__ void __launch_bounds__(WPB * 32, kWarpsPerSM / WPB)
+template <int WPB, bool LOCK, int WPSM>
+__global__ void __launch_bounds__(WPB * 32, WPSM / WPB)
 step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4* __restrict__ meta,
             const uint16_t* __restrict__ pairs, float* __restrict__ qg, float* __restrict__ vg,
             float* __restrict__ sg, unsigned* __restrict__ status, Counters* __restrict__ counters,

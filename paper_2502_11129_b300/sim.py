@@ -37,6 +37,7 @@ class SimConfig(C.Structure):
         ("ground", C.c_int32), ("box_box", C.c_int32), ("actuate", C.c_int32),
         ("max_correct_vel", C.c_float), ("device", C.c_int32), ("stream", C.c_uint64), ("steps_per_launch", C.c_int32),
         ("warps_per_block", C.c_int32), ("min_cfm", C.c_float), ("phase_lock", C.c_int32),
+        ("warps_per_sm", C.c_int32),
     ]
 
 
@@ -65,7 +66,7 @@ class Counters(C.Structure):
 DEFAULTS = dict(dt=0.002, gravity=(0.0, 0.0, -9.81), pgs_iters=30, soft_tau=0.02, soft_zeta=1.0,
                 mu=1.0, contact_cap=64, kp=2.0, kd=0.05, tau_max=1.0, theta_max=np.pi / 2,
                 armature=1e-4, ground=1, box_box=1, actuate=1, max_correct_vel=0.1, device=0, stream=0,
-                steps_per_launch=0, warps_per_block=0, min_cfm=0.1, phase_lock=0)
+                steps_per_launch=0, warps_per_block=0, min_cfm=0.1, phase_lock=0, warps_per_sm=0)
 
 _lib = None
 
@@ -97,7 +98,7 @@ def lib():
         L.sim_step_n_noalloc.argtypes = [P(SimConfig), P(DevicePopulation), C.c_int32]
         L.sim_debug_sincos.argtypes = [vp, C.c_int32, vp, vp]
         L.sim_robot_cost.argtypes = [vp, vp, C.c_int32]
-        L.sim_launch_shape.argtypes = [vp, vp, vp, vp]
+        L.sim_launch_shape.argtypes = [vp, vp, vp, vp, vp]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
@@ -261,10 +262,13 @@ class Sim:
                     a=rows[:m, 7].astype(np.int32), b=bb[:m])
 
     def launch_shape(self) -> dict:
-        """Launch shape in use (warps per block, phase lock, steps per launch)."""
-        w, lk, spl = C.c_int32(), C.c_int32(), C.c_int32()
-        self._check(lib().sim_launch_shape(self.h, C.byref(w), C.byref(lk), C.byref(spl)), "sim_launch_shape")
-        return dict(warps_per_block=w.value, phase_lock=lk.value, steps_per_launch=spl.value)
+        """Launch shape in use (warps per block, phase lock, steps per launch,
+        resident warps per SM)."""
+        w, lk, spl, occ = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(lib().sim_launch_shape(self.h, C.byref(w), C.byref(lk), C.byref(spl), C.byref(occ)),
+                    "sim_launch_shape")
+        return dict(warps_per_block=w.value, phase_lock=lk.value, steps_per_launch=spl.value,
+                    warps_per_sm=occ.value)
 
     def robot_cost(self):
         """SM cycles per step of every robot in the last launch (caller order)."""

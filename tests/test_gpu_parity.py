@@ -274,25 +274,39 @@ def test_autotune_keeps_state():
     a.autotune(20)
     q1, v1, _, _ = a.read_state()
     assert np.array_equal(q1, Q) and np.array_equal(v1, V)
+    shape = a.launch_shape()
+    assert shape["warps_per_sm"] in (12, 16) and shape["warps_per_block"] in (1, 2, 4, 8)
+    assert not (shape["warps_per_sm"] == 12 and shape["warps_per_block"] == 8)
     a.step(30)
     b = _gpu_sim(pop, warps_per_block=1)
     b.set_state(Q, V, Sx)
     b.step(30)
     assert np.array_equal(a.read_state()[0], b.read_state()[0])
+    # a configured register budget is kept by the autotuner
+    c = _gpu_sim(pop, warps_per_sm=12)
+    c.set_state(Q, V, Sx)
+    c.autotune(20)
+    assert c.launch_shape()["warps_per_sm"] == 12
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        S.Sim(warps_per_sm=12, warps_per_block=8)
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        S.Sim(warps_per_sm=10)
 
 
 def test_launch_shapes_and_phase_lock_agree_bitwise():
     """Warps per block, phase-locked blocks (with idle warps in the last
-    block and a frozen robot that keeps taking the barriers) and the
-    slowest-first launch order change only the schedule: every robot's state
-    is bitwise the same."""
+    block and a frozen robot that keeps taking the barriers), the register
+    budget (16 or 12 resident warps per SM) and the slowest-first launch
+    order change only the schedule: every robot's state is bitwise the
+    same."""
     pop = P.grammar(203, seed=47).as_float32()
     s0 = P.cpg_initial(pop)
     Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, s0)
     V[5, 8] = np.nan  # robot 5 freezes at its first step
     ref = None
-    for wpb, lock in ((1, 0), (2, 1), (4, 0), (4, 1), (8, 1)):
-        sm = _gpu_sim(pop, warps_per_block=wpb, phase_lock=lock, steps_per_launch=25)
+    for wpb, lock, occ in ((1, 0, 16), (2, 1, 16), (4, 0, 16), (4, 1, 16), (8, 1, 16), (1, 0, 12), (2, 1, 12),
+                           (4, 0, 12)):
+        sm = _gpu_sim(pop, warps_per_block=wpb, phase_lock=lock, warps_per_sm=occ, steps_per_launch=25)
         sm.set_state(Q, V, Sx)
         sm.step(60)
         out = sm.read_state()
@@ -302,7 +316,7 @@ def test_launch_shapes_and_phase_lock_agree_bitwise():
             ref = out
         else:
             for a, b in zip(ref, out):
-                assert np.array_equal(a, b, equal_nan=True), (wpb, lock)
+                assert np.array_equal(a, b, equal_nan=True), (wpb, lock, occ)
 
 
 def test_one_step_largest_robots_26_bodies():
