@@ -46,20 +46,28 @@ struct __align__(16) WarpSmem {
   float r[3][32];          // body frame origins relative to the core origin
   float c[3][32];          // box centres relative to the core origin
   float S[6][32];          // dof-indexed motion subspace columns
+  // one region, four lifetimes within a step: the dynamics' accumulators,
+  // then the contact generation's near pairs and kept-candidate masks, then
+  // the contact rows and the Delassus matrix
   union {
     float acc[16][33];     // per-body f (6) + composite inertia (10), padded (steps 1-4)
+    struct {
+      uint16_t nearp[kMaxPairs];  // near body pairs of the step, (a << 8) | b (step 6)
+      unsigned keep[kCand / 32];  // candidates kept under the cap (step 6)
+    };
     float Yt[32][32];      // contact rows under construction, [dof][row] (step 7),
                            // then the Delassus matrix [row][row] (step 8)
   };
   float M[kTri];           // mass matrix, then its Cholesky factor (packed lower)
   float invd[32];
   float vfree[32];
-  int parent[32];
+  int8_t parent[32];
   unsigned path[32];
-  unsigned keep[kCand / 32];
-  uint16_t nearp[kMaxPairs];       // near box/box pairs of the step, (a << 8) | b
   unsigned long long ph[kPhases];  // per-phase SM cycles (inspection only)
 };
+// 16 warps of this (plus the 1 KB the SM reserves per block) fit a 164 KB
+// shared-memory carve-out, which leaves the rest of the SM's 256 KB to L1
+static_assert(16 * (sizeof(WarpSmem) + 1024) <= 164 * 1024, "per-warp shared memory");
 
 __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFull, x, src); }
 __device__ __forceinline__ int shfi(int x, int src) { return __shfl_sync(kFull, x, src); }
