@@ -165,6 +165,25 @@ int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n);
 int sim_set_state(sim_ctx_t* ctx, int32_t first, int32_t count, const float* q,
                   const float* v, const float* cpg);
 
+/* Device-buffer variants of sim_set_state, sim_read_state and sim_fitness,
+ * for callers whose data already lives on the GPU (e.g. torch tensors via
+ * their data pointers): same row layouts and rules, but every buffer is
+ * caller-owned device (or managed) memory of cfg->device, nothing is copied
+ * through the host and nothing synchronises.  The work is queued on the
+ * context stream (sim_stream): inputs must be ready before it runs (written
+ * on that stream, or ordered by an event the caller makes it wait on) and
+ * stay unchanged, and outputs valid, until the stream has passed the call.
+ * A buffer that is not device memory of that device is rejected with
+ * SIM_EINVAL.  Outputs that are NULL are skipped. */
+int sim_set_state_dev(sim_ctx_t* ctx, int32_t first, int32_t count, const float* q, const float* v,
+                      const float* cpg);
+int sim_read_state_dev(sim_ctx_t* ctx, int32_t first, int32_t count, float* q, float* v, float* cpg,
+                       uint32_t* status);
+int sim_fitness_dev(sim_ctx_t* ctx, float* out, int32_t n);
+
+/* The context's stream (a cudaStream_t) into *stream. */
+int sim_stream(const sim_ctx_t* ctx, uint64_t* stream);
+
 /* Advance every variant n_steps (>= 0) steps.  Asynchronous on the context
  * stream (a captured CUDA graph per distinct n_steps); launch errors are
  * returned, execution errors surface at the next synchronising call. */

@@ -709,6 +709,74 @@ int sim_fitness(sim_ctx_t* ctx, float* out, int32_t n) {
   return SIM_OK;
 }
 
+// a caller buffer for the _dev entry points: device (or managed) memory
+// reachable from the context's device, or NULL where allowed
+static bool dev_ptr_ok(const sim_ctx_t* ctx, const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == ctx->cfg.device;
+}
+
+int sim_set_state_dev(sim_ctx_t* ctx, int32_t first, int32_t count, const float* q, const float* v,
+                      const float* cpg) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_set_state_dev: no population");
+  if (!q || !v || first < 0 || count < 0 || first + count > ctx->n)
+    return fail(ctx, SIM_EINVAL, "sim_set_state_dev: bad range or NULL q/v");
+  if (count == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (!dev_ptr_ok(ctx, q) || !dev_ptr_ok(ctx, v) || !dev_ptr_ok(ctx, cpg))
+    return fail(ctx, SIM_EINVAL, "sim_set_state_dev: a buffer is not device memory of the context's device");
+  scatter_state<<<count, 64, 0, ctx->stream>>>(q, v, cpg, ctx->d_perm, first, count, cpg ? 1 : 0, ctx->d_q,
+                                               ctx->d_v, ctx->d_s, ctx->d_fit0, ctx->d_status);
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
+
+int sim_read_state_dev(sim_ctx_t* ctx, int32_t first, int32_t count, float* q, float* v, float* cpg,
+                       uint32_t* status) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_read_state_dev: no population");
+  if (first < 0 || count < 0 || first + count > ctx->n)
+    return fail(ctx, SIM_EINVAL, "sim_read_state_dev: bad range");
+  if (count == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (!dev_ptr_ok(ctx, q) || !dev_ptr_ok(ctx, v) || !dev_ptr_ok(ctx, cpg) || !dev_ptr_ok(ctx, status))
+    return fail(ctx, SIM_EINVAL, "sim_read_state_dev: a buffer is not device memory of the context's device");
+  // outputs the caller does not want land in the staging area
+  float* dq = ctx->d_stage;
+  float* dv = dq + (size_t)count * SIM_QW;
+  float* ds = dv + (size_t)count * SIM_VW;
+  gather_state<<<count, 64, 0, ctx->stream>>>(ctx->d_q, ctx->d_v, ctx->d_s, ctx->d_status, ctx->d_perm, first,
+                                              count, q ? q : dq, v ? v : dv, cpg ? cpg : ds,
+                                              status ? status : ctx->d_stage_st);
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
+
+int sim_fitness_dev(sim_ctx_t* ctx, float* out, int32_t n) {
+  if (!ctx) return SIM_EINVAL;
+  if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_fitness_dev: no population");
+  if (!out || n < 0 || n > ctx->n) return fail(ctx, SIM_EINVAL, "sim_fitness_dev: bad n or NULL out");
+  if (n == 0) return SIM_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (!dev_ptr_ok(ctx, out))
+    return fail(ctx, SIM_EINVAL, "sim_fitness_dev: out is not device memory of the context's device");
+  fitness_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_q, ctx->d_fit0, ctx->d_perm, n, out);
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
+
+int sim_stream(const sim_ctx_t* ctx, uint64_t* stream) {
+  if (!ctx || !stream) return SIM_EINVAL;
+  *stream = reinterpret_cast<uint64_t>(ctx->stream);
+  return SIM_OK;
+}
+
 int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
   if (!ctx) return SIM_EINVAL;
   if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_autotune: no population");

@@ -25,7 +25,8 @@ STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: 
 
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
            "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
-           "sim_debug_contacts", "sim_debug_solver", "sim_debug_sincos", "sim_robot_cost", "sim_launch_shape", "sim_step_n_noalloc", "sim_last_error"]
+           "sim_debug_contacts", "sim_debug_solver", "sim_debug_sincos", "sim_robot_cost", "sim_launch_shape", "sim_step_n_noalloc", "sim_set_state_dev", "sim_read_state_dev",
+           "sim_fitness_dev", "sim_stream", "sim_last_error"]
 
 
 class SimConfig(C.Structure):
@@ -99,6 +100,10 @@ def lib():
         L.sim_debug_sincos.argtypes = [vp, C.c_int32, vp, vp]
         L.sim_robot_cost.argtypes = [vp, vp, C.c_int32]
         L.sim_launch_shape.argtypes = [vp, vp, vp, vp, vp]
+        L.sim_set_state_dev.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.sim_read_state_dev.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp]
+        L.sim_fitness_dev.argtypes = [vp, vp, C.c_int32]
+        L.sim_stream.argtypes = [vp, C.POINTER(C.c_uint64)]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
@@ -235,6 +240,30 @@ class Sim:
         self._check(lib().sim_read_state(self.h, first, count, C.c_void_p(q_ptr), C.c_void_p(v_ptr),
                                          C.c_void_p(s_ptr) if s_ptr else None,
                                          C.c_void_p(st_ptr) if st_ptr else None), "sim_read_state")
+
+    def set_state_dev(self, first, count, q_ptr, v_ptr, s_ptr=0):
+        """Device pointers (e.g. CUDA torch tensors' data_ptr()) with the ABI
+        strides; queued on the context stream, no synchronisation."""
+        self._check(lib().sim_set_state_dev(self.h, first, count, C.c_void_p(q_ptr), C.c_void_p(v_ptr),
+                                            C.c_void_p(s_ptr) if s_ptr else None), "sim_set_state_dev")
+
+    def read_state_dev(self, first, count, q_ptr=0, v_ptr=0, s_ptr=0, st_ptr=0):
+        """Device-pointer outputs (0 = skip); queued on the context stream."""
+        vp = lambda x: C.c_void_p(x) if x else None
+        self._check(lib().sim_read_state_dev(self.h, first, count, vp(q_ptr), vp(v_ptr), vp(s_ptr), vp(st_ptr)),
+                    "sim_read_state_dev")
+
+    def fitness_dev(self, out_ptr, n: int | None = None):
+        """Fitness of variants [0, n) into a device buffer; queued on the context stream."""
+        n = self.n if n is None else n
+        self._check(lib().sim_fitness_dev(self.h, C.c_void_p(out_ptr), n), "sim_fitness_dev")
+
+    @property
+    def stream(self) -> int:
+        """The context's cudaStream_t as an integer (e.g. for torch.cuda.ExternalStream)."""
+        s = C.c_uint64()
+        self._check(lib().sim_stream(self.h, C.byref(s)), "sim_stream")
+        return s.value
 
     def fitness(self, n: int | None = None):
         n = self.n if n is None else n

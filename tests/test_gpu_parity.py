@@ -471,3 +471,42 @@ def test_heavy_cubes_rest_on_the_softness_floor_on_gpu():
     dstar = 0.1 * (100.0 * G * dt / 4) * dt / erp
     assert (gst & 5).sum() == 0
     assert np.abs(gq[:, 2] - (0.05 - dstar)).max() < 1e-6
+
+
+def test_device_buffer_state_transfers_match_host_ones():
+    """sim_set_state_dev / sim_read_state_dev / sim_fitness_dev with CUDA
+    torch tensors give bitwise the results of the host-buffer calls, and a
+    host pointer is refused."""
+    import torch
+    pop = P.grammar(77, seed=91).as_float32()
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+    a = _gpu_sim(pop)
+    a.set_state(Q, V, Sx)
+    a.step(40)
+    qa, va, sa, sta = a.read_state()
+    fa = a.fitness()
+    b = _gpu_sim(pop)
+    dev = torch.device("cuda", 0)
+    tq, tv, ts = (torch.from_numpy(x).to(dev) for x in (Q, V, Sx))
+    torch.cuda.synchronize()
+    b.set_state_dev(0, pop.n, tq.data_ptr(), tv.data_ptr(), ts.data_ptr())
+    b.step(40)
+    oq = torch.zeros_like(tq)
+    ov = torch.zeros_like(tv)
+    os_ = torch.zeros_like(ts)
+    ost = torch.zeros(pop.n, dtype=torch.int32, device=dev)
+    of = torch.zeros(pop.n, dtype=torch.float32, device=dev)
+    b.read_state_dev(0, pop.n, oq.data_ptr(), ov.data_ptr(), os_.data_ptr(), ost.data_ptr())
+    b.fitness_dev(of.data_ptr())
+    ext = torch.cuda.ExternalStream(b.stream, device=dev)
+    ext.synchronize()
+    assert np.array_equal(oq.cpu().numpy(), qa) and np.array_equal(ov.cpu().numpy(), va)
+    assert np.array_equal(os_.cpu().numpy(), sa)
+    assert np.array_equal(ost.cpu().numpy().view(np.uint32), sta)
+    assert np.array_equal(of.cpu().numpy(), fa)
+    # a part of the population, and a host buffer refused
+    b.read_state_dev(10, 5, q_ptr=oq.data_ptr())
+    ext.synchronize()
+    assert np.array_equal(oq[:5].cpu().numpy(), qa[10:15])
+    with pytest.raises(S.SimError, match="SIM_EINVAL"):
+        b.set_state_dev(0, 2, Q.ctypes.data, V.ctypes.data)
