@@ -1,18 +1,16 @@
 // b3sur.cu -- learned fitness surrogate: BF16 MLP 128 -> 256 -> 256 -> 1 on
-// tensor cores (forward layers: tcgen05.mma with the accumulator in tensor
-// memory; backward GEMMs with strided operands: mma.sync m16n8k16; FP32
-// accumulation throughout), Adam on FP32 master weights, GPU genotype
-// encoding and top-k selection.
+// the tcgen05 tensor cores (TMA-fed, accumulator in tensor memory, FP32
+// accumulation), Adam on FP32 master weights, GPU genotype encoding and top-k
+// selection.
 //
-// The forward layers (row-major operands, 128-row tiles, N = 256) run on
-// gemm_umma (TMA + tcgen05), whose epilogue is fused with the layer's bias +
-// ReLU.  The
-// backward GEMMs run on gemm_bf16, a strided kernel C(m, n) = sum_k A(m, k)
-// B(n, k) that also computes the weight gradients by reducing over the batch
-// (strided operands instead of transposed copies).  Weights and inputs are
+// Every dense layer, forward and backward, runs on one GEMM kernel,
+// gemm_umma: C(m, n) = sum over operand pairs of A(m, k) B(n, k) with both
+// operands K-major, the forward epilogue fused with the layer's bias + ReLU.
+// The weight gradients reduce over the batch, so their operands are first
+// copied transposed (K = the batch along a row).  Weights and inputs are
 // BF16; activations and backward operands are carried as BF16 pairs (value =
-// hi + lo, both BF16) and the GEMMs run over both parts, so only the weights
-// and inputs are rounded to 8 mantissa bits.
+// hi + lo, both BF16) and the GEMMs accumulate over both parts, so only the
+// weights and inputs are rounded to 8 mantissa bits.
 #include <cuda.h>  // CUtensorMap and its enums (the driver entry point is fetched at run time)
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -22,6 +20,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -42,140 +41,65 @@ constexpr int OB2 = OW2 + HID * HID;
 constexpr int OW3 = OB2 + HID;
 constexpr int OB3 = OW3 + HID;
 
-// epilogues: store FP32, add to FP32, or bias + ReLU + BF16 (hi, lo) split
-enum Epi { EPI_F32 = 0, EPI_F32_ADD = 1, EPI_BIAS_RELU_BF16 = 2 };
-
-// strided GEMM of the backward pass (EPI_F32 or EPI_F32_ADD)
-struct GemmArgs {
-  int M, N, K;
-  const bf16* A;
-  long lam, lak;  // A(m, k) = A[m * lam + k * lak]
-  const bf16* B;
-  long lbn, lbk;  // B(n, k) = B[n * lbn + k * lbk]
-  float* Cf;
-  long ldc;
-  int epi;
-};
-
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// 64 x 64 block tile, K step 32, 4 warps of 32 x 32 (2 x 4 MMA tiles each)
-__global__ void __launch_bounds__(128) gemm_bf16(GemmArgs g) {
-  __shared__ __align__(16) bf16 As[64][40];
-  __shared__ __align__(16) bf16 Bs[64][40];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int gid = lane >> 2, tig = lane & 3;
-  const bf16 zero = __float2bfloat16(0.f);
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  for (int k0 = 0; k0 < g.K; k0 += 32) {
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-      const int e = tid + 128 * j;
-      int mm, kk;
-      if (g.lak == 1) { mm = e >> 5; kk = e & 31; } else { kk = e >> 6; mm = e & 63; }
-      const int m = m0 + mm, k = k0 + kk;
-      As[mm][kk] = (m < g.M && k < g.K) ? g.A[(long)m * g.lam + (long)k * g.lak] : zero;
-      int nn, kb;
-      if (g.lbk == 1) { nn = e >> 5; kb = e & 31; } else { kb = e >> 6; nn = e & 63; }
-      const int n = n0 + nn, kq = k0 + kb;
-      Bs[nn][kb] = (n < g.N && kq < g.K) ? g.B[(long)n * g.lbn + (long)kq * g.lbk] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < 32; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int r = wm + mi * 16 + gid;
-        af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
-        af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
-        af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
-        af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
-      }
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int c = wn + ni * 8 + gid;
-        bfr[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2]);
-        bfr[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2 + 8]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = m0 + wm + mi * 16 + gid + 8 * (i >> 1);
-        const int col = n0 + wn + ni * 8 + tig * 2 + (i & 1);
-        if (row >= g.M || col >= g.N) continue;
-        const float v = acc[mi][ni][i];
-        const long o = (long)row * g.ldc + col;
-        if (g.epi == EPI_F32_ADD) g.Cf[o] += v;
-        else g.Cf[o] = v;
-      }
-}
+// epilogues: store FP32, or bias + ReLU + BF16 (hi, lo) split
+enum Epi { EPI_F32 = 0, EPI_BIAS_RELU_BF16 = 1 };
 
 // ---------------------------------------------------------------------------
-// Forward dense layers on the tcgen05 tensor cores, fed by TMA.
+// Dense layers on the tcgen05 tensor cores, fed by TMA.
 //
-// C(m, n) = sum over parts p of sum_k A_p(m, k) W(n, k) for a tile of 128 rows
-// and all HID = 256 outputs per CTA.  K runs in chunks of 64 through a
-// two-stage shared-memory ring.  One thread produces and issues: per chunk it
-// arms the stage's `full` mbarrier with the chunk's byte count and starts 16
-// tensor copies (cp.async.bulk.tensor.2d), each an 8-element K slice of 128 A
-// rows (2 KB) or 256 W rows (4 KB); a box of 8 BF16 x rows lands as rows x 16 B,
-// which is the no-swizzle K-major core-matrix layout with 8-row groups 128 B
-// apart and K-adjacent core matrices one slice apart.  Once a stage is full it
-// issues the chunk's four tcgen05.mma (M 128, N 256, K 16; BF16 operands, FP32
-// accumulator in tensor memory) and commits them to the stage's `empty`
-// mbarrier, then refills the stage the previous chunk used as soon as that
-// chunk's MMAs have drained it, so copies overlap the tensor core.  A last
-// commit to the `done` mbarrier releases the epilogue: tcgen05.ld (thread =
-// row, 16 columns at a time) with bias + ReLU + the BF16 (hi, lo) split, or an
-// FP32 store.  Every wait has an iteration limit; a give-up sets a device flag
-// that the host checks after its next synchronisation.
-constexpr int UM_M = 128, UM_N = HID, UM_KC = 64, UM_STAGES = 2;
-constexpr int UM_A_SLICE = UM_M * 16, UM_B_SLICE = UM_N * 16;            // bytes per 8-wide K slice
-constexpr int UM_A_STAGE = UM_A_SLICE * (UM_KC / 8), UM_B_STAGE = UM_B_SLICE * (UM_KC / 8);
-constexpr int UM_STAGE = UM_A_STAGE + UM_B_STAGE;                          // 48 KB
-// requested dynamic shared memory: at most two CTAs per SM, so their 2 x 256
-// tensor-memory columns always fit the SM's 512 and an allocation never waits
+// C(m, n) = sum over parts p of sum_k A_p(m, k) B_p(n, k) for a tile of 128
+// rows and all BN (256 or 128) columns per CTA; every operand is K-major
+// (row-major with K contiguous: the forward activations and weights as they
+// are, the backward operands through transposed copies).  K runs in chunks of
+// 64 through a two-stage shared-memory ring.  One thread produces and issues:
+// per chunk it arms the stage's `full` mbarrier with the chunk's byte count
+// and starts 16 tensor copies (cp.async.bulk.tensor.2d), each an 8-element K
+// slice of 128 A rows or BN B rows (2 KB / BN x 16 B); a box of 8 BF16 x rows
+// lands as rows x 16 B, which is the no-swizzle K-major core-matrix layout
+// with 8-row groups 128 B apart and K-adjacent core matrices one slice apart.
+// Once a stage is full it issues the chunk's four tcgen05.mma (M 128, N BN,
+// K 16; BF16 operands, FP32 accumulator in tensor memory) and commits them to
+// the stage's `empty` mbarrier, then refills the stage the previous chunk
+// used as soon as that chunk's MMAs have drained it, so copies overlap the
+// tensor core.  A last commit to the `done` mbarrier releases the epilogue:
+// tcgen05.ld (thread = row, 16 columns at a time) with bias + ReLU + the BF16
+// (hi, lo) split, or an FP32 store.  Every wait has an iteration limit; a
+// give-up sets a device flag that the host checks after its next
+// synchronisation.
+constexpr int UM_M = 128, UM_KC = 64, UM_STAGES = 2, UM_MAXPARTS = 3;
+constexpr int UM_A_SLICE = UM_M * 16;  // bytes per 8-wide K slice of A
+// requested dynamic shared memory: at most two CTAs per SM, so their tensor-
+// memory columns (at most 2 x 256) always fit the SM's 512 and an
+// allocation never waits
 constexpr int UM_SMEM = 100 * 1024;
 constexpr unsigned UM_SPIN = 1u << 22;
-static_assert(UM_STAGES * UM_STAGE <= UM_SMEM, "the ring fits the shared memory");
-// kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A (bit 7)
-// and B (bit 10), both K-major, N / 8 at bit 17, M / 16 at bit 24
-constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_N >> 3) << 17) |
-                              ((uint32_t)(UM_M >> 4) << 24);
+template <int BN>
+struct UmmaShape {
+  static constexpr int B_SLICE = BN * 16;
+  static constexpr int A_STAGE = UM_A_SLICE * (UM_KC / 8), B_STAGE = B_SLICE * (UM_KC / 8);
+  static constexpr int STAGE = A_STAGE + B_STAGE;
+  // kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A (bit 7)
+  // and B (bit 10), both K-major, N / 8 at bit 17, M / 16 at bit 24
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(UM_M >> 4) << 24);
+  static_assert(UM_STAGES * STAGE <= UM_SMEM, "the ring fits the shared memory");
+};
 
 struct UmmaArgs {
-  int M, K, parts;   // K a multiple of UM_KC; parts 1 or 2 (A maps 0 and 1)
+  int M, K, parts;   // K a multiple of UM_KC; parts 1..UM_MAXPARTS operand pairs
   const float* bias; // EPI_BIAS_RELU_BF16
-  float* Cf;         // EPI_F32 output, row stride UM_N
-  bf16* Cb;          // EPI_BIAS_RELU_BF16 outputs (hi, lo), row stride UM_N
+  float* Cf;         // EPI_F32 output, row stride BN
+  bf16* Cb;          // EPI_BIAS_RELU_BF16 outputs (hi, lo), row stride BN
   bf16* Cb_lo;
   int epi;
   int* err;          // set to 1 when a wait gives up
+};
+
+// the operand pairs' tensor maps (a kernel parameter: the maps live in the
+// parameter space the copies read them from)
+struct UmmaMaps {
+  CUtensorMap a[UM_MAXPARTS];
+  CUtensorMap b[UM_MAXPARTS];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -207,9 +131,9 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int
       : "memory");
 }
 
-__global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtensorMap mA0,
-                                                 const __grid_constant__ CUtensorMap mA1,
-                                                 const __grid_constant__ CUtensorMap mW, UmmaArgs g) {
+template <int BN>
+__global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ UmmaMaps maps, UmmaArgs g) {
+  using Sh = UmmaShape<BN>;
   extern __shared__ __align__(1024) unsigned char um_smem[];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed;
@@ -218,7 +142,7 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
   const int m0 = blockIdx.x * UM_M;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(UM_N));
+                 "r"(BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -238,13 +162,12 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
   if (tid == 0) {
     const uint32_t ring = smem_u32(um_smem);
     auto load = [&](int c) {
-      const int s = c % UM_STAGES, k0 = (c % nk) * UM_KC;
-      const CUtensorMap* ma = (c / nk) ? &mA1 : &mA0;
-      const uint32_t a = ring + s * UM_STAGE, b = a + UM_A_STAGE, bar = smem_u32(&full_bar[s]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(UM_STAGE) : "memory");
+      const int s = c % UM_STAGES, part = c / nk, k0 = (c % nk) * UM_KC;
+      const uint32_t a = ring + s * Sh::STAGE, b = a + Sh::A_STAGE, bar = smem_u32(&full_bar[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(Sh::STAGE) : "memory");
       for (int j = 0; j < UM_KC / 8; ++j) {
-        tma_2d(a + j * UM_A_SLICE, ma, k0 + 8 * j, m0, bar);
-        tma_2d(b + j * UM_B_SLICE, &mW, k0 + 8 * j, 0, bar);
+        tma_2d(a + j * UM_A_SLICE, &maps.a[part], k0 + 8 * j, m0, bar);
+        tma_2d(b + j * Sh::B_SLICE, &maps.b[part], k0 + 8 * j, 0, bar);
       }
     };
     bool ok = true;
@@ -255,15 +178,15 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
       ok = mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((c / UM_STAGES) & 1));
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a = ring + s * UM_STAGE, b = a + UM_A_STAGE;
+      const uint32_t a = ring + s * Sh::STAGE, b = a + Sh::A_STAGE;
 #pragma unroll
       for (int ks = 0; ks < UM_KC / 16; ++ks) {
         const uint32_t acc = (c | ks) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(tmem),
-            "l"(umma_desc(a + 2 * ks * UM_A_SLICE, UM_A_SLICE)), "l"(umma_desc(b + 2 * ks * UM_B_SLICE, UM_B_SLICE)),
-            "r"(UM_IDESC), "r"(acc));
+            "l"(umma_desc(a + 2 * ks * UM_A_SLICE, UM_A_SLICE)),
+            "l"(umma_desc(b + 2 * ks * Sh::B_SLICE, Sh::B_SLICE)), "r"(Sh::IDESC), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&empty_bar[s]))
@@ -292,7 +215,7 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
   } else {
     const int row = m0 + 32 * warp + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < UM_N; c0 += 16) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
       asm volatile(
@@ -303,7 +226,7 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row >= g.M) continue;
       if (g.epi == EPI_F32) {
-        float4* o = reinterpret_cast<float4*>(g.Cf + (size_t)row * UM_N + c0);
+        float4* o = reinterpret_cast<float4*>(g.Cf + (size_t)row * BN + c0);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
@@ -316,8 +239,8 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
           hi[j] = __float2bfloat16(x);
           lo[j] = __float2bfloat16(x - __bfloat162float(hi[j]));
         }
-        uint4* oh = reinterpret_cast<uint4*>(g.Cb + (size_t)row * UM_N + c0);
-        uint4* ol = reinterpret_cast<uint4*>(g.Cb_lo + (size_t)row * UM_N + c0);
+        uint4* oh = reinterpret_cast<uint4*>(g.Cb + (size_t)row * BN + c0);
+        uint4* ol = reinterpret_cast<uint4*>(g.Cb_lo + (size_t)row * BN + c0);
         oh[0] = reinterpret_cast<const uint4*>(hi)[0];
         oh[1] = reinterpret_cast<const uint4*>(hi)[1];
         ol[0] = reinterpret_cast<const uint4*>(lo)[0];
@@ -327,7 +250,25 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ CUtenso
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_N));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+// dst[c][r] = src[r][c] for r < rows (valid rows), 0 for rows <= r < rows_pad;
+// dst has row stride ld_dst (the transposed operands' K runs along a row)
+__global__ void transpose_pad(const bf16* __restrict__ src, int rows, int cols, int rows_pad, bf16* __restrict__ dst,
+                              long ld_dst) {
+  __shared__ bf16 t[32][34];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    t[k][tx] = (r < rows && c < cols) ? src[(size_t)r * cols + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (c < cols && r < rows_pad) dst[(size_t)c * ld_dst + r] = t[tx][k];
+  }
 }
 
 // h = relu(z + b) as FP32 and as a BF16 pair (hi, lo)
@@ -401,26 +342,46 @@ __global__ void relu_mask_split(float* __restrict__ dz, const bf16* __restrict__
 }
 
 // column sums over the batch: gb2, gW3 (from dy, W3, H2 in FP32) and gb1
-// (from the FP32 dZ1), gb3
+// (from the FP32 dZ1) per block of 32 columns x 8 batch-row lanes; the last
+// block sums dy for gb3.  Partial sums are combined in a fixed order.
 __global__ void col_sums(const float* __restrict__ dy, const bf16* __restrict__ W3, const float* __restrict__ H2,
                          const float* __restrict__ dZ1, int n, float* grads) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < HID) {
-    float b2 = 0.f, w3 = 0.f, b1 = 0.f;
+  __shared__ float part[3][8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float b2 = 0.f, w3 = 0.f, b1 = 0.f;
+  if (blockIdx.x < HID / 32) {
+    const int j = blockIdx.x * 32 + tx;
     const float w3j = __bfloat162float(W3[j]);
-    for (int m = 0; m < n; ++m) {
+    for (int m = ty; m < n; m += 8) {
       const float h = H2[(long)m * HID + j];
       b2 += h > 0.f ? dy[m] * w3j : 0.f;
       w3 += dy[m] * h;
       b1 += dZ1[(long)m * HID + j];
     }
-    grads[OB2 + j] = b2;
-    grads[OW3 + j] = w3;
-    grads[OB1 + j] = b1;
-  } else if (j == HID) {
-    float s = 0.f;
-    for (int m = 0; m < n; ++m) s += dy[m];
-    grads[OB3] = s;
+  } else {
+    for (int m = ty * 32 + tx; m < n; m += 256) b2 += dy[m];
+  }
+  part[0][ty][tx] = b2;
+  part[1][ty][tx] = w3;
+  part[2][ty][tx] = b1;
+  __syncthreads();
+  if (ty != 0) return;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int r = 0; r < 8; ++r) {
+    s0 += part[0][r][tx];
+    s1 += part[1][r][tx];
+    s2 += part[2][r][tx];
+  }
+  if (blockIdx.x < HID / 32) {
+    const int j = blockIdx.x * 32 + tx;
+    grads[OB2 + j] = s0;
+    grads[OW3 + j] = s1;
+    grads[OB1 + j] = s2;
+  } else {
+    // the 32 lanes' sums of dy, in lane order
+    float t = 0.f;
+    for (int l = 0; l < 32; ++l) t += __shfl_sync(0xffffffffu, s0, l);
+    if (tx == 0) grads[OB3] = t;
   }
 }
 
@@ -636,7 +597,19 @@ struct sur_ctx {
   int* idx = nullptr;
   size_t cap_scores = 0;
   int* uerr = nullptr;     // set by gemm_umma when a tensor-core wait gives up
-  CUtensorMap tm_x{}, tm_h1{}, tm_h1lo{}, tm_w1{}, tm_w2{};  // TMA maps of the forward operands
+  // K-major (transposed) copies of the backward operands: [column][batch row],
+  // row stride SUR_MAX_BATCH, batch rows padded with zeros to a multiple of 64
+  bf16* dz2T = nullptr;
+  bf16* dz2loT = nullptr;
+  bf16* h1T = nullptr;
+  bf16* h1loT = nullptr;
+  bf16* dz1T = nullptr;
+  bf16* dz1loT = nullptr;
+  bf16* xT = nullptr;
+  bf16* w2T = nullptr;     // W2 transposed (HID x HID)
+  // TMA maps: A operands in boxes of 8 x 128 rows, B operands in boxes of 8 x N rows
+  CUtensorMap tm_x{}, tm_h1{}, tm_h1lo{}, tm_dz2{}, tm_dz2lo{}, tm_dz2T{}, tm_dz2loT{}, tm_dz1T{}, tm_dz1loT{};
+  CUtensorMap tm_w1{}, tm_w2{}, tm_w2T{}, tm_h1T{}, tm_h1loT{}, tm_xT{};
 };
 
 namespace {
@@ -659,9 +632,9 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, count * sizeof(T));
 }
 
-cudaError_t launch_gemm(cudaStream_t st, const GemmArgs& g) {
-  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
-  gemm_bf16<<<grid, 128, 0, st>>>(g);
+cudaError_t transpose(cudaStream_t st, const bf16* src, int rows, int cols, int rows_pad, bf16* dst, long ld_dst) {
+  dim3 grid((rows_pad + 31) / 32, (cols + 31) / 32), block(32, 8);
+  transpose_pad<<<grid, block, 0, st>>>(src, rows, cols, rows_pad, dst, ld_dst);
   return cudaGetLastError();
 }
 
@@ -669,6 +642,24 @@ cudaError_t refresh_bf16(sur_ctx* c) {
   to_bf16<<<(HID * IN + 255) / 256, 256, 0, c->stream>>>(c->p + OW1, c->w1b, HID * IN);
   to_bf16<<<(HID * HID + 255) / 256, 256, 0, c->stream>>>(c->p + OW2, c->w2b, HID * HID);
   to_bf16<<<1, 256, 0, c->stream>>>(c->p + OW3, c->w3b, HID);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return transpose(c->stream, c->w2b, HID, HID, HID, c->w2T, HID);
+}
+
+template <int BN>
+cudaError_t launch_umma(sur_ctx* c, int M, int K, std::initializer_list<const CUtensorMap*> a,
+                        std::initializer_list<const CUtensorMap*> b, UmmaArgs g) {
+  UmmaMaps maps{};
+  int p = 0;
+  for (const CUtensorMap* m : a) maps.a[p++] = *m;
+  p = 0;
+  for (const CUtensorMap* m : b) maps.b[p++] = *m;
+  g.M = M;
+  g.K = K;
+  g.parts = p;
+  g.err = c->uerr;
+  gemm_umma<BN><<<(M + UM_M - 1) / UM_M, 128, UM_SMEM, c->stream>>>(maps, g);
   return cudaGetLastError();
 }
 
@@ -678,18 +669,13 @@ cudaError_t refresh_bf16(sur_ctx* c) {
 cudaError_t forward_batch(sur_ctx* c, int n) {
   // layer 1: H1 = relu(X W1^T + b1) as a BF16 pair; layer 2: Z2 = (H1 + H1lo) W2^T
   // with both parts accumulated in one tensor-memory accumulator
-  const int grid = (n + UM_M - 1) / UM_M;
   UmmaArgs g{};
-  g.M = n; g.K = IN; g.parts = 1;
-  g.bias = c->p + OB1; g.Cb = c->h1; g.Cb_lo = c->h1lo; g.epi = EPI_BIAS_RELU_BF16; g.err = c->uerr;
-  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(c->tm_x, c->tm_x, c->tm_w1, g);
-  cudaError_t e = cudaGetLastError();
+  g.bias = c->p + OB1; g.Cb = c->h1; g.Cb_lo = c->h1lo; g.epi = EPI_BIAS_RELU_BF16;
+  cudaError_t e = launch_umma<HID>(c, n, IN, {&c->tm_x}, {&c->tm_w1}, g);
   if (e != cudaSuccess) return e;
   UmmaArgs h{};
-  h.M = n; h.K = HID; h.parts = 2;
-  h.Cf = c->z2f; h.epi = EPI_F32; h.err = c->uerr;
-  gemm_umma<<<grid, 128, UM_SMEM, c->stream>>>(c->tm_h1, c->tm_h1lo, c->tm_w2, h);
-  e = cudaGetLastError();
+  h.Cf = c->z2f; h.epi = EPI_F32;
+  e = launch_umma<HID>(c, n, HID, {&c->tm_h1, &c->tm_h1lo}, {&c->tm_w2, &c->tm_w2}, h);
   if (e != cudaSuccess) return e;
   bias_relu_split<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->z2f, c->p + OB2, n, c->h2f, c->h2,
                                                                            c->h2lo);
@@ -703,42 +689,41 @@ cudaError_t forward_batch(sur_ctx* c, int n) {
 // ~2^-16 instead of BF16's 2^-8.
 cudaError_t backward_batch(sur_ctx* c, int n) {
   const int nblk = (n + 255) / 256;
+  const int kp = (n + UM_KC - 1) / UM_KC * UM_KC;  // batch padded to whole K chunks
+  const long ld = SUR_MAX_BATCH;
   loss_grad<<<nblk, 256, 0, c->stream>>>(c->y, c->tb, n, c->dy, c->part);
   dz2_kernel<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->dy, c->w3b, c->h2f, n, c->dz2, c->dz2lo);
-  cudaError_t e;
-  // dW2(i, j) = sum_m dZ2(m, i) H1(m, j): hi*hi + lo*hi + hi*lo
-  for (int part = 0; part < 3; ++part) {
-    GemmArgs g{};
-    g.M = HID; g.N = HID; g.K = n;
-    g.A = part == 1 ? c->dz2lo : c->dz2; g.lam = 1; g.lak = HID;
-    g.B = part == 2 ? c->h1lo : c->h1; g.lbn = 1; g.lbk = HID;
-    g.Cf = c->g + OW2; g.ldc = HID; g.epi = part ? EPI_F32_ADD : EPI_F32;
-    e = launch_gemm(c->stream, g);
-    if (e != cudaSuccess) return e;
-  }
-  // dH1(m, j) = sum_i dZ2(m, i) W2(i, j), in FP32 (hi part, then lo part added)
-  for (int part = 0; part < 2; ++part) {
-    GemmArgs h{};
-    h.M = n; h.N = HID; h.K = HID;
-    h.A = part ? c->dz2lo : c->dz2; h.lam = HID; h.lak = 1;
-    h.B = c->w2b; h.lbn = 1; h.lbk = HID;
-    h.Cf = c->dz1f; h.ldc = HID; h.epi = part ? EPI_F32_ADD : EPI_F32;
-    e = launch_gemm(c->stream, h);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = cudaGetLastError();
+  // K-major copies for the weight gradients (K = the batch)
+  if (e == cudaSuccess) e = transpose(c->stream, c->dz2, n, HID, kp, c->dz2T, ld);
+  if (e == cudaSuccess) e = transpose(c->stream, c->dz2lo, n, HID, kp, c->dz2loT, ld);
+  if (e == cudaSuccess) e = transpose(c->stream, c->h1, n, HID, kp, c->h1T, ld);
+  if (e == cudaSuccess) e = transpose(c->stream, c->h1lo, n, HID, kp, c->h1loT, ld);
+  if (e == cudaSuccess) e = transpose(c->stream, c->xb, n, IN, kp, c->xT, ld);
+  if (e != cudaSuccess) return e;
+  // dW2(i, j) = sum_m dZ2(m, i) H1(m, j): hi*hi + lo*hi + hi*lo in one accumulator
+  UmmaArgs g{};
+  g.Cf = c->g + OW2; g.epi = EPI_F32;
+  e = launch_umma<HID>(c, HID, kp, {&c->tm_dz2T, &c->tm_dz2loT, &c->tm_dz2T}, {&c->tm_h1T, &c->tm_h1T, &c->tm_h1loT},
+                       g);
+  if (e != cudaSuccess) return e;
+  // dH1(m, j) = sum_i dZ2(m, i) W2(i, j): both parts of dZ2 against W2 transposed
+  UmmaArgs h{};
+  h.Cf = c->dz1f; h.epi = EPI_F32;
+  e = launch_umma<HID>(c, n, HID, {&c->tm_dz2, &c->tm_dz2lo}, {&c->tm_w2T, &c->tm_w2T}, h);
+  if (e != cudaSuccess) return e;
   relu_mask_split<<<(int)(((long)n * HID + 255) / 256), 256, 0, c->stream>>>(c->dz1f, c->h1, c->h1lo, n, c->dz1,
                                                                            c->dz1lo);
-  // dW1(i, j) = sum_m dZ1(m, i) X(m, j)
-  for (int part = 0; part < 2; ++part) {
-    GemmArgs w{};
-    w.M = HID; w.N = IN; w.K = n;
-    w.A = part ? c->dz1lo : c->dz1; w.lam = 1; w.lak = HID;
-    w.B = c->xb; w.lbn = 1; w.lbk = IN;
-    w.Cf = c->g + OW1; w.ldc = IN; w.epi = part ? EPI_F32_ADD : EPI_F32;
-    e = launch_gemm(c->stream, w);
-    if (e != cudaSuccess) return e;
-  }
-  col_sums<<<(HID + 1 + 127) / 128, 128, 0, c->stream>>>(c->dy, c->w3b, c->h2f, c->dz1f, n, c->g);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = transpose(c->stream, c->dz1, n, HID, kp, c->dz1T, ld);
+  if (e == cudaSuccess) e = transpose(c->stream, c->dz1lo, n, HID, kp, c->dz1loT, ld);
+  if (e != cudaSuccess) return e;
+  // dW1(i, j) = sum_m dZ1(m, i) X(m, j): both parts of dZ1
+  UmmaArgs w{};
+  w.Cf = c->g + OW1; w.epi = EPI_F32;
+  e = launch_umma<IN>(c, HID, kp, {&c->tm_dz1T, &c->tm_dz1loT}, {&c->tm_xT, &c->tm_xT}, w);
+  if (e != cudaSuccess) return e;
+  col_sums<<<HID / 32 + 1, dim3(32, 8), 0, c->stream>>>(c->dy, c->w3b, c->h2f, c->dz1f, n, c->g);
   return cudaGetLastError();
 }
 
@@ -780,7 +765,7 @@ int ensure_scores(sur_ctx* ctx, size_t n) {
 void free_all(sur_ctx* c) {
   void* ptrs[] = {c->p, c->g, c->m, c->v, c->w1b, c->w2b, c->w3b, c->xb, c->h1, c->h2, c->dz2, c->dz1,
                   c->dz2lo, c->dz1lo, c->h1lo, c->h2lo, c->h2f, c->z2f, c->dz1f, c->y, c->dy, c->tb, c->part, c->xfull, c->tfull, c->perm, c->topk_work, c->scores,
-                  c->idx, c->uerr};
+                  c->idx, c->uerr, c->dz2T, c->dz2loT, c->h1T, c->h1loT, c->dz1T, c->dz1loT, c->xT, c->w2T};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -890,11 +875,23 @@ int sur_create(const sur_config* cfg, sur_ctx_t** out) {
             dalloc(&ctx->dy, B) == cudaSuccess && dalloc(&ctx->tb, B) == cudaSuccess &&
             dalloc(&ctx->part, (B + 255) / 256) == cudaSuccess &&
             dalloc(&ctx->topk_work, (size_t)2 * SUR_MAX_TOPK) == cudaSuccess && dalloc(&ctx->uerr, 1) == cudaSuccess &&
+            dalloc(&ctx->dz2T, (size_t)HID * B) == cudaSuccess && dalloc(&ctx->dz2loT, (size_t)HID * B) == cudaSuccess &&
+            dalloc(&ctx->h1T, (size_t)HID * B) == cudaSuccess && dalloc(&ctx->h1loT, (size_t)HID * B) == cudaSuccess &&
+            dalloc(&ctx->dz1T, (size_t)HID * B) == cudaSuccess && dalloc(&ctx->dz1loT, (size_t)HID * B) == cudaSuccess &&
+            dalloc(&ctx->xT, (size_t)IN * B) == cudaSuccess && dalloc(&ctx->w2T, (size_t)HID * HID) == cudaSuccess &&
             cudaMemset(ctx->uerr, 0, sizeof(int)) == cudaSuccess &&
-            cudaFuncSetAttribute(gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
+            cudaFuncSetAttribute(gemm_umma<HID>, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
+            cudaFuncSetAttribute(gemm_umma<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
+            // A operands (boxes of 128 rows)
             make_map(&ctx->tm_x, ctx->xb, B, IN, UM_M) && make_map(&ctx->tm_h1, ctx->h1, B, HID, UM_M) &&
-            make_map(&ctx->tm_h1lo, ctx->h1lo, B, HID, UM_M) && make_map(&ctx->tm_w1, ctx->w1b, HID, IN, UM_N) &&
-            make_map(&ctx->tm_w2, ctx->w2b, HID, HID, UM_N);
+            make_map(&ctx->tm_h1lo, ctx->h1lo, B, HID, UM_M) && make_map(&ctx->tm_dz2, ctx->dz2, B, HID, UM_M) &&
+            make_map(&ctx->tm_dz2lo, ctx->dz2lo, B, HID, UM_M) && make_map(&ctx->tm_dz2T, ctx->dz2T, HID, B, UM_M) &&
+            make_map(&ctx->tm_dz2loT, ctx->dz2loT, HID, B, UM_M) && make_map(&ctx->tm_dz1T, ctx->dz1T, HID, B, UM_M) &&
+            make_map(&ctx->tm_dz1loT, ctx->dz1loT, HID, B, UM_M) &&
+            // B operands (boxes of N rows)
+            make_map(&ctx->tm_w1, ctx->w1b, HID, IN, HID) && make_map(&ctx->tm_w2, ctx->w2b, HID, HID, HID) &&
+            make_map(&ctx->tm_w2T, ctx->w2T, HID, HID, HID) && make_map(&ctx->tm_h1T, ctx->h1T, HID, B, HID) &&
+            make_map(&ctx->tm_h1loT, ctx->h1loT, HID, B, HID) && make_map(&ctx->tm_xT, ctx->xT, IN, B, IN);
   if (!ok) {
     free_all(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
