@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -278,12 +279,16 @@ cudaError_t cost_order(const LaunchArgs& a) {
 template <int WPB, bool LOCK, int WPSM>
 cudaError_t launch_wpb(const LaunchArgs& a, int nsteps) {
   const size_t sm = smem_bytes(WPB);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(b3::step_kernel<WPB, LOCK, WPSM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // the shared-memory attribute is per device: set it once on each device used
+  constexpr int kMaxDevices = 64;
+  static std::atomic<bool> attr_done[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices || !attr_done[dev].load(std::memory_order_acquire)) {
+    e = cudaFuncSetAttribute(b3::step_kernel<WPB, LOCK, WPSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    if (dev >= 0 && dev < kMaxDevices) attr_done[dev].store(true, std::memory_order_release);
   }
   dim3 grid((a.n + WPB - 1) / WPB), block(32 * WPB);
   b3::step_kernel<WPB, LOCK, WPSM><<<grid, block, sm, a.stream>>>(a.mf, a.mi, a.meta, a.pairs, a.q, a.v, a.s,
