@@ -16,6 +16,7 @@
 #include "b3cpu.h"
 #include "model_pack.h"
 #include "step_common.cuh"
+#include "free_body.cuh"
 
 using namespace b3;
 
@@ -622,9 +623,16 @@ int cpu_step_n(cpu_ctx_t* ctx, int32_t n_steps) {
       unsigned st = ctx->status[k];
       unsigned long long nc = 0;
       const auto t0 = std::chrono::steady_clock::now();
-      for (int t = 0; t < n_steps && !(st & 5u); ++t)
-        step_robot(m, ctx->pk.pairs.data(), ctx->P, &ctx->q[(size_t)k * 32], &ctx->v[(size_t)k * 32],
-                   &ctx->s[(size_t)k * 64], st, nc, *w);
+      if (free_body_eligible(m.nb, m.F + F_COM * 32)) {
+        // a single free body: the one-body closed form of the step
+        FreeBodyOut fo;
+        for (int t = 0; t < n_steps && !(st & 5u); ++t)
+          if (free_body_step(m.F, ctx->P, &ctx->q[(size_t)k * 32], &ctx->v[(size_t)k * 32], st, fo)) nc += fo.nc;
+      } else {
+        for (int t = 0; t < n_steps && !(st & 5u); ++t)
+          step_robot(m, ctx->pk.pairs.data(), ctx->P, &ctx->q[(size_t)k * 32], &ctx->v[(size_t)k * 32],
+                     &ctx->s[(size_t)k * 64], st, nc, *w);
+      }
       ctx->seconds[k] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       ctx->status[k] = st;
       ctx->contacts[k] += nc;

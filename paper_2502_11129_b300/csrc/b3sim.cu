@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "b3sim.h"
+#include "free_body.cuh"
 #include "model_pack.h"
 #include "step_kernel.cuh"
 
@@ -35,6 +36,7 @@ struct sim_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int n = 0;
+  int n_free = 0;         // single free bodies, the last packed robots (one-body step)
   std::vector<int> perm;  // packed index -> caller index
   std::vector<int> inv;   // caller index -> packed index
   float* d_mf = nullptr;
@@ -177,10 +179,68 @@ struct LaunchArgs {
   int* lastnc;
   int* order;          // NULL: slot = packed index
   unsigned* order_hist;
-  int n;
+  int n;               // robots of the warp-per-robot step: packed [0, n)
   StepParams P;
   cudaStream_t stream;
+  int n_free;          // single free bodies after them: packed [n, n + n_free)
 };
+
+// One thread per single free body (a box or a sphere whose centre is its
+// frame origin): the one-body closed form of the step (free_body.cuh) for
+// nsteps steps, with the same per-robot state, status, counters and
+// inspection block as the warp-per-robot kernel.
+__global__ void __launch_bounds__(128) free_body_kernel(const float* __restrict__ mf, float* __restrict__ qg,
+                                                        float* __restrict__ vg, unsigned* __restrict__ status,
+                                                        b3::Counters* __restrict__ counters,
+                                                        float* __restrict__ scratch, int* __restrict__ last_nc,
+                                                        int first, int count, int nsteps, b3::StepParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int var = first + i;
+  const float* F = mf + (size_t)var * b3::NF * 32;
+  float* qv = qg + (size_t)var * 32;
+  float* vv = vg + (size_t)var * 32;
+  float q[7], v[6];
+  for (int k = 0; k < 7; ++k) q[k] = qv[k];
+  for (int k = 0; k < 6; ++k) v[k] = vv[k];
+  unsigned st = status[var];
+  unsigned long long n_contacts = 0, n_steps = 0;
+  b3::FreeBodyOut fo;
+  fo.nc = last_nc[var];
+  const long long t0 = clock64();
+  for (int t = 0; t < nsteps && !(st & 5u); ++t) {
+    if (b3::free_body_step(F, P, q, v, st, fo)) {
+      n_contacts += (unsigned)fo.nc;
+      ++n_steps;
+    }
+  }
+  const long long cyc = clock64() - t0;
+  for (int k = 0; k < 7; ++k) qv[k] = q[k];
+  for (int k = 0; k < 6; ++k) vv[k] = v[k];
+  status[var] = st;
+  b3::Counters c = counters[var];
+  c.contacts += n_contacts;
+  c.steps += n_steps;
+  c.cycles += (unsigned long long)cyc;
+  counters[var] = c;
+  if (n_steps == 0) return;
+  last_nc[var] = fo.nc;
+  // the last step's contacts (candidate layout) and inspection block
+  float* cand = scratch + (size_t)var * b3::kScratchFloats;
+  for (int k = 0; k < fo.nc; ++k) {
+    float* row = cand + (size_t)k * b3::kCandW;
+    row[0] = fo.p[k][0]; row[1] = fo.p[k][1]; row[2] = fo.p[k][2];
+    row[3] = 0.f; row[4] = 0.f; row[5] = 1.f;
+    row[6] = fo.depth[k];
+    row[7] = __int_as_float(0 | (255 << 8));
+  }
+  float* dbg = cand + b3::kDbgOffset;
+  for (int k = 0; k < 32; ++k) dbg[k] = k < 6 ? fo.vfree[k] : 0.f;
+  dbg[31] = (float)cyc / (float)n_steps;
+  for (int k = 0; k < fo.nc; ++k)
+    for (int t = 0; t < 3; ++t) dbg[32 + 4 * k + t] = fo.lam[k][t];
+  for (int k = 0; k < b3::kPhases; ++k) dbg[32 + 4 * b3::kCapMax + k] = 0.f;
+}
 
 // Slowest-first scheduling.  A launch lasts as long as its slowest robot, and
 // robots differ in cost by an order of magnitude (bodies, contacts, near
@@ -324,12 +384,22 @@ cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb, bool lock, in
 
 cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool lock, int wpsm, int spl) {
   for (int done = 0; done < n_steps; done += spl) {
-    if (a.order) {
-      cudaError_t e = cost_order(a);
+    const int chunk = std::min(spl, n_steps - done);
+    if (a.n > 0) {
+      if (a.order) {
+        cudaError_t e = cost_order(a);
+        if (e != cudaSuccess) return e;
+      }
+      cudaError_t e = launch_chunk(a, chunk, wpb, lock, wpsm);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_chunk(a, std::min(spl, n_steps - done), wpb, lock, wpsm);
-    if (e != cudaSuccess) return e;
+    if (a.n_free > 0) {
+      free_body_kernel<<<(a.n_free + 127) / 128, 128, 0, a.stream>>>(a.mf, a.q, a.v, a.status, a.counters,
+                                                                      a.scratch, a.lastnc, a.n, a.n_free, chunk,
+                                                                      a.P);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -337,7 +407,8 @@ cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool loc
 LaunchArgs ctx_args(sim_ctx* ctx) {
   return LaunchArgs{ctx->d_mf,     ctx->d_mi,    ctx->d_meta,   ctx->d_pairs,       ctx->d_q,
                     ctx->d_v,      ctx->d_s,     ctx->d_status, ctx->d_counters,    ctx->d_scratch,
-                    ctx->d_lastnc, ctx->d_order, ctx->d_order_hist, ctx->n, ctx->P, ctx->stream};
+                    ctx->d_lastnc, ctx->d_order, ctx->d_order_hist, ctx->n - ctx->n_free, ctx->P, ctx->stream,
+                    ctx->n_free};
 }
 
 cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int wpsm, int spl) {
@@ -493,7 +564,7 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
   if (e == cudaSuccess) {
     LaunchArgs args{pop->model_f, pop->model_i, reinterpret_cast<const int4*>(pop->meta), pop->pairs,
                     pop->q,       pop->v,       pop->cpg, pop->status, a.counters, a.scratch, a.lastnc,
-                    nullptr,      nullptr,      pop->n,   make_params(cfg), stream};
+                    nullptr,      nullptr,      pop->n,   make_params(cfg), stream, 0};
     const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
     const int wpsm = cfg->warps_per_sm > 0 ? cfg->warps_per_sm : 16;
     const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : kDefaultStepsPerLaunch;
@@ -579,6 +650,7 @@ int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
   std::vector<int4> meta(n);
   for (int k = 0; k < n; ++k) meta[k] = make_int4(pk.meta[4 * k], pk.meta[4 * k + 1], pk.meta[4 * k + 2], pk.meta[4 * k + 3]);
   ctx->n = n;
+  ctx->n_free = pk.n_free;
   ctx->perm = perm;
   ctx->inv = inv;
   const size_t N = (size_t)n;

@@ -2,7 +2,7 @@
 // population (host code shared by the GPU simulator and the CPU engine).
 //
 // Layout per packed robot k (robots sorted by body count, largest first,
-// stable): float fields [NF][32 body slots], int fields [NI][32], meta
+// stable; single free bodies with their centre at the frame origin last): float fields [NF][32 body slots], int fields [NI][32], meta
 // (bodies, tree depth, pair count, pair offset) and the list of body/body
 // candidate pairs (a < b, a not the parent of b, not excluded), each packed
 // as (a << 8) | b.
@@ -20,6 +20,7 @@
 namespace b3 {
 
 struct PackedPopulation {
+  int n_free = 0;         // single free bodies (free_body.cuh), packed last
   std::vector<int> perm;  // packed index -> caller index
   std::vector<int> inv;   // caller index -> packed index
   std::vector<float> mf;
@@ -72,11 +73,21 @@ inline std::string validate_population(const sim_variant_desc* v, int n, const c
 }
 
 inline void pack_population(const sim_variant_desc* v, int n, PackedPopulation& out) {
-  // pack in size order (largest first, stable)
+  // pack in size order (largest first, stable), the single free bodies that
+  // the one-body step serves last of all
+  auto is_free = [&](int i) {
+    return v[i].n_bodies == 1 && v[i].box_center[0] == 0.f && v[i].box_center[1] == 0.f &&
+           v[i].box_center[2] == 0.f;
+  };
   std::vector<int>& perm = out.perm;
   perm.resize(n);
   std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return v[a].n_bodies > v[b].n_bodies; });
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+    if (v[a].n_bodies != v[b].n_bodies) return v[a].n_bodies > v[b].n_bodies;
+    return !is_free(a) && is_free(b);
+  });
+  out.n_free = 0;
+  for (int i = 0; i < n; ++i) out.n_free += is_free(i) ? 1 : 0;
   std::vector<int>& inv = out.inv;
   inv.assign(n, 0);
   for (int k = 0; k < n; ++k) inv[perm[k]] = k;

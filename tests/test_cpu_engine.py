@@ -318,3 +318,26 @@ def test_rolling_ball_closed_form():
     acc = (v[:, 0] - v0) / (400 * 0.002)
     assert np.abs(acc - 5.0 / 7.0 * G * np.sin(a)).max() < 0.01 * G * np.sin(a)
     assert np.abs(v[:, 0] - v[:, 4] * r).max() < 0.01 * np.abs(v[:, 0]).min()
+
+
+def test_one_step_single_free_bodies():
+    """Robots that are one free body (cubes, balls) take the one-body closed
+    form of the step: tumbling cubes pressed into the ground (1-8 vertices,
+    gyroscopic torque), the same with a contact cap of 3, and free balls,
+    each against the oracle."""
+    pop = P.boxes(64, seed=7, vel_sigma=2.0)
+    rng = np.random.default_rng(8)
+    q = pop.q0.copy()
+    q[:, 2] = rng.uniform(0.0, 0.09, pop.n)
+    errs, near, ost, gst = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)))
+    _check(errs, near, 0.1)
+    assert np.array_equal(ost[~near], gst[~near])
+    errs, near, ost, gst = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)), contact_cap=3)
+    _check(errs, near, 0.1)
+    assert ((gst & 2) != 0).sum() >= 5
+    balls = P.boxes(32, seed=9, vel_sigma=2.0)
+    balls.geom[:, 0] = P.GEOM_SPHERE
+    qb = balls.q0.copy()
+    qb[:, 2] = rng.uniform(0.03, 0.06, balls.n)
+    errs, near, ost, gst = _one_step(balls, qb, balls.v0, np.zeros((balls.n, 64)))
+    _check(errs, near, 0.1)

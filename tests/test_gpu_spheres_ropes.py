@@ -153,3 +153,69 @@ def test_ropes_contact_free_and_contact_rich():
     print("rope mean fitness gpu %.6f oracle %.6f" % (gf.mean(), of.mean()))
     assert (st & 5).sum() == 0 and (ost & 5).sum() == 0
     assert abs(gf.mean() - of.mean()) <= 0.02 * of.mean()
+
+
+def test_single_free_bodies_on_the_one_body_kernel():
+    """Cubes and balls alone take the thread-per-robot kernel: tumbling cubes
+    pressed into the ground (with and without a contact cap of 3) and free
+    balls against the oracle, one step from the same states."""
+    pop = P.boxes(96, seed=7, vel_sigma=2.0)
+    rng = np.random.default_rng(8)
+    q = pop.q0.copy()
+    q[:, 2] = rng.uniform(0.0, 0.09, pop.n)
+    for cap in (64, 3):
+        errs, margins, ost, gst, _ = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)), contact_cap=cap)
+        near, bad, msg = _report(f"free-cubes-cap{cap}", errs, margins)
+        assert not bad.any(), msg
+        assert near.mean() < 0.1, msg
+        assert np.array_equal(ost[~near], gst[~near])
+    balls = P.boxes(64, seed=9, vel_sigma=2.0)
+    balls.geom[:, 0] = P.GEOM_SPHERE
+    qb = balls.q0.copy()
+    qb[:, 2] = rng.uniform(0.03, 0.06, balls.n)
+    errs, margins, ost, gst, _ = _one_step(balls, qb, balls.v0, np.zeros((balls.n, 64)))
+    near, bad, msg = _report("free-balls", errs, margins)
+    assert not bad.any(), msg
+
+
+def _concat(a, b):
+    import dataclasses
+    fields = {}
+    for f in dataclasses.fields(a):
+        x, y = getattr(a, f.name), getattr(b, f.name)
+        fields[f.name] = np.concatenate([x, y]) if isinstance(x, np.ndarray) else x
+    fields["n"] = a.n + b.n
+    return P.Population(**fields)
+
+
+def test_mixed_population_runs_both_kernels_bitwise():
+    """A population mixing free cubes and grammar robots steps each robot
+    exactly as a population of its own kind does (the cubes on the
+    thread-per-robot kernel, the rest on the warp-per-robot kernel), and the
+    contact lists of the cubes match the oracle's."""
+    O = oracle()
+    cubes = P.boxes(40, seed=11)
+    robots = P.grammar(30, seed=12)
+    mixed = _concat(robots, cubes).as_float32()
+    runs = {}
+    for name, pop in (("mixed", mixed), ("robots", robots.as_float32()), ("cubes", cubes.as_float32())):
+        Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+        sm = _gpu_sim(pop, warps_per_block=1)
+        sm.set_state(Q, V, Sx)
+        sm.step(299)
+        before = sm.read_state()[0]
+        sm.step(1)
+        runs[name] = (sm.read_state(), sm, before)
+    (qm, vm, sm_, stm), smm, q299 = runs["mixed"]
+    assert np.array_equal(qm[:30], runs["robots"][0][0]) and np.array_equal(vm[:30], runs["robots"][0][1])
+    assert np.array_equal(qm[30:], runs["cubes"][0][0]) and np.array_equal(vm[30:], runs["cubes"][0][1])
+    checked = 0
+    for i in range(30, 70):
+        m = O.model_from_population(mixed, i)
+        c = O.contacts(m, q299[i, :O.nq(m)].astype(np.float64))
+        if c["margin"] < MARGIN:
+            continue
+        g = smm.debug_contacts(i)
+        assert g["n"] == len(c["a"]) and np.allclose(g["depth"], c["depth"], atol=1e-5), i
+        checked += 1
+    assert checked > 20
