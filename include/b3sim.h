@@ -6,8 +6,9 @@
  * *variants* of a robot scene for a fixed number of steps, on the CPU and on
  * the GPU, and (Sec. 6) splits the variants between the two.  This library is
  * that engine for one GPU: every variant is an articulated modular robot (a
- * core cube plus hinge-jointed cubic bricks, or a single free box) on a
- * ground plane, and one call advances the whole population by n steps.
+ * core cube plus hinge-jointed cubic bricks or balls, or a single free box or
+ * ball) on a ground plane, and one call advances the whole population by n
+ * steps.
  * Each step, per variant, in this order:
  *   1. CPG controller: s <- s + dt W s (W antisymmetric from the per-hinge
  *      weights), hinge torque tau = clamp(kp (theta_max clamp(x,-1,1) - theta)
@@ -18,9 +19,10 @@
  *   4. joint-space inertia M(q) by the composite-rigid-body algorithm plus a
  *      hinge armature;
  *   5. Cholesky M = L L^T and v_free = v + dt M^-1 (tau - c);
- *   6. contacts: box/plane vertices; box/box separating-axis test with face
- *      clipping or an edge-edge point; at most contact_cap contacts (the
- *      deepest, in list order);
+ *   6. contacts: box/plane vertices, a sphere's lowest point; box/box
+ *      separating-axis test with face clipping or an edge-edge point,
+ *      sphere/box and sphere/sphere at one point; at most contact_cap
+ *      contacts (the deepest, in list order);
  *   7. soft projected Gauss-Seidel over the contact impulses (ERP/CFM soft
  *      constraints, penetration recovery speed capped at max_correct_vel,
  *      disk friction cone, pgs_iters sweeps, list order);

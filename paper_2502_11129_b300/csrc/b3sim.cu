@@ -2,10 +2,12 @@
 //
 // The library owns every device buffer.  A population is packed once into a
 // structure-of-arrays model (per variant: [field][32 body slots]), sorted by
-// robot size so that the warps of a launch carry similar work and the largest
-// robots start first.  Steps run as persistent launches of step_kernel (one
-// warp per robot, many steps per launch); the launch sequence for a given
-// step count is captured once in a CUDA graph and replayed.
+// robot size, with the robots that are one free body (centred on their frame
+// origin) last.  Steps run as persistent launches of step_kernel (one warp
+// per robot, many steps per launch, slowest robots first) and of
+// free_body_kernel for the single free bodies (one thread per robot); the
+// launch sequence for a given step count is captured once in a CUDA graph and
+// replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
