@@ -31,13 +31,15 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // global scratch per variant: candidate rows, the narrow phase's per-lane
 // staging rows, Y rows (32 floats each), the Gauss-Seidel constants of each
-// contact (kCstW floats: b, 1/(A+R), R of its three rows, then the
-// normal-tangent couplings A_t1n, A_t2n), then the last step's v_free and
-// impulses (inspection only)
+// contact (kCstG floats: b, 1/(A+R), R of its three rows, the normal-tangent
+// couplings A_t1n, A_t2n, a zero, then the 3 x 3 block B_k = Y_(k+1) Y_k^T
+// that couples it to the next contact of the sweep, row-major, and three
+// zeros), then the last step's v_free and impulses (inspection only)
+constexpr int kCstG = 24;
 constexpr size_t kStageOffset = (size_t)kCand * kCandW;            // 32 lanes x 8 points x 8 floats
 constexpr size_t kYOffset = kStageOffset + (size_t)32 * 8 * kCandW;
 constexpr size_t kCstOffset = kYOffset + (size_t)kYRows * 32;
-constexpr size_t kDbgOffset = kCstOffset + (size_t)kCapMax * kCstW;
+constexpr size_t kDbgOffset = kCstOffset + (size_t)kCapMax * kCstG;
 constexpr int kPhases = 10;  // per-phase cycle counters (inspection only)
 constexpr size_t kScratchFloats = kDbgOffset + 32 + 4 * kCapMax + 16;
 
@@ -733,7 +735,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         const float inv = aa > kAmin ? 1.f / (aa + Rr) : 0.f;
         // penetration recovery speed, capped (ODE's maximum correcting velocity)
         const float bias = dir == 0 ? jv - fminf(P.erp * depth_k / dt, P.max_correct_vel) : jv;
-        float* cs = cstg + (size_t)k * kCstW + 3 * dir;
+        float* cs = cstg + (size_t)k * kCstG + 3 * dir;
         cs[0] = bias;
         cs[1] = inv;
         cs[2] = Rr;
@@ -741,24 +743,48 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       __syncwarp();
     }
-    // tangent/normal coupling A_tn = Y_t . Y_n of each contact (lane = contact)
+    // tangent/normal coupling A_tn = Y_t . Y_n of each contact (lane =
+    // contact), and for the dof-space sweep (more than 10 contacts) the block
+    // B_k = Y_(k+1) Y_k^T to the next contact in sweep order
+    const bool dofspace = 3 * nc > 32;
     for (int k0 = 0; k0 < nc; k0 += 32) {
       const int k = k0 + lane;
       if (k < nc) {
         const float4* yn = reinterpret_cast<const float4*>(Yg + (size_t)(3 * k) * 32);
         const float4* y1 = yn + 8;
         const float4* y2 = yn + 16;
+        const int kn = (k + 1 < nc) ? k + 1 : 0;
+        const float4* zn = reinterpret_cast<const float4*>(Yg + (size_t)(3 * kn) * 32);
         float a1 = 0.f, a2 = 0.f;
+        float b[9];
 #pragma unroll
+        for (int t = 0; t < 9; ++t) b[t] = 0.f;
+#pragma unroll 1
         for (int i = 0; i < 8; ++i) {
           const float4 n4 = yn[i], p4 = y1[i], q4 = y2[i];
           a1 += p4.x * n4.x + p4.y * n4.y + p4.z * n4.z + p4.w * n4.w;
           a2 += q4.x * n4.x + q4.y * n4.y + q4.z * n4.z + q4.w * n4.w;
+          if (dofspace) {
+            const float4 ys[3] = {n4, p4, q4};
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+              const float4 z4 = zn[8 * t + i];
+#pragma unroll
+              for (int s2 = 0; s2 < 3; ++s2)
+                b[3 * t + s2] += z4.x * ys[s2].x + z4.y * ys[s2].y + z4.z * ys[s2].z + z4.w * ys[s2].w;
+            }
+          }
         }
-        float* cs = cstg + (size_t)k * kCstW;
+        float4* cs4 = reinterpret_cast<float4*>(cstg + (size_t)k * kCstG);
+        float* cs = cstg + (size_t)k * kCstG;
         cs[9] = a1;
         cs[10] = a2;
         cs[11] = 0.f;
+        if (dofspace) {
+          cs4[3] = make_float4(b[0], b[1], b[2], b[3]);
+          cs4[4] = make_float4(b[4], b[5], b[6], b[7]);
+          cs4[5] = make_float4(b[8], 0.f, 0.f, 0.f);
+        }
       }
     }
 #pragma unroll
@@ -776,6 +802,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       // a contact update reads its three residuals with shuffles and adds
       // A_r. dlam to every row.  Same iteration as the dof-space sweep below.
       {
+        // columns 0 .. 4 nq4 - 1 cover the 3 nc rows; the sweep reads no other
+        const int nq4 = (3 * nc + 3) >> 2;
         float a[32];
 #pragma unroll
         for (int c2 = 0; c2 < 32; ++c2) a[c2] = 0.f;
@@ -785,96 +813,150 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           const float4* Yj = reinterpret_cast<const float4*>(sm.Yt[j]);
 #pragma unroll
           for (int q4 = 0; q4 < 8; ++q4) {
-            const float4 y4 = Yj[q4];
-            a[4 * q4] += own * y4.x;
-            a[4 * q4 + 1] += own * y4.y;
-            a[4 * q4 + 2] += own * y4.z;
-            a[4 * q4 + 3] += own * y4.w;
+            if (q4 < nq4) {
+              const float4 y4 = Yj[q4];
+              a[4 * q4] += own * y4.x;
+              a[4 * q4 + 1] += own * y4.y;
+              a[4 * q4 + 2] += own * y4.z;
+              a[4 * q4 + 3] += own * y4.w;
+            }
           }
         }
         __syncwarp();
 #pragma unroll
-        for (int c2 = 0; c2 < 32; ++c2) sm.Yt[c2][lane] = a[c2];  // [col][row], symmetric
+        for (int q4 = 0; q4 < 8; ++q4) {
+          if (q4 < nq4) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) sm.Yt[4 * q4 + t][lane] = a[4 * q4 + t];  // [col][row], symmetric
+          }
+        }
         __syncwarp();
       }
-      float lam = 0.f, w = w_row;
-      const float4* c4 = reinterpret_cast<const float4*>(cstg);
-      float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
-      float an = sm.Yt[0][lane], a1 = sm.Yt[1][lane], a2 = sm.Yt[2][lane];
-      for (int it = 0; it < P.iters; ++it) {
-        for (int k = 0; k < nc; ++k) {
-          const int kn = (k + 1 < nc) ? k + 1 : 0;
-          const float nan0 = sm.Yt[3 * kn][lane], na1 = sm.Yt[3 * kn + 1][lane], na2 = sm.Yt[3 * kn + 2][lane];
-          const float4 na = c4[3 * kn], nb4 = c4[3 * kn + 1], nc4 = c4[3 * kn + 2];
-          const int r = 3 * k;
-          const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
-          const float ln = shf(lam, r), l1 = shf(lam, r + 1), l2 = shf(lam, r + 2);
-          const float gn = wn + ca.z * ln;
-          const float lnn = fmaxf(0.f, ln - gn * ca.y);
-          const float dn = lnn - ln;
-          const float g1 = w1 + cc4.y * dn + cb4.y * l1;
-          const float g2 = w2 + cc4.z * dn + cc4.x * l2;
-          float l1t = l1 - g1 * cb4.x;
-          float l2t = l2 - g2 * cb4.w;
-          const float lim = P.mu * lnn;
-          const float nt2 = l1t * l1t + l2t * l2t;
-          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
-          l1t *= sc;
-          l2t *= sc;
-          w += an * dn + a1 * (l1t - l1) + a2 * (l2t - l2);
-          lam = lane == r ? lnn : (lane == r + 1 ? l1t : (lane == r + 2 ? l2t : lam));
-          an = nan0; a1 = na1; a2 = na2;
-          ca = na; cb4 = nb4; cc4 = nc4;
-        }
+      // Staging in the rotation rows of shared memory (free during the
+      // sweep): the Gauss-Seidel constants of every contact and the
+      // impulses of every contact, which all lanes compute alike and store
+      // alike, so each lane later reads back its own write.
+      float4* lamS = reinterpret_cast<float4*>(&sm.R[0][0]);
+      float4* cS = lamS + 12;
+      {
+        const float4* c4 = reinterpret_cast<const float4*>(cstg);
+        if (lane < 3 * nc) cS[lane] = c4[2 * lane - lane % 3];  // 3 of the 6 float4 of each contact
+        if (lane < nc) lamS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      __syncwarp();
+      float w = w_row;
+      float4 ca = cS[0], cb4 = cS[1], cc4 = cS[2];
+      float an = sm.Yt[0][lane], a1 = sm.Yt[1][lane], a2 = sm.Yt[2][lane];
+      float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of the contact being updated
+      const int nupd = P.iters * nc;
+      int k = 0;
+#pragma unroll 2
+      for (int upd = 0; upd < nupd; ++upd) {
+        const int kn = (k + 1 < nc) ? k + 1 : 0;
+        const float nan0 = sm.Yt[3 * kn][lane], na1 = sm.Yt[3 * kn + 1][lane], na2 = sm.Yt[3 * kn + 2][lane];
+        const float4 na = cS[3 * kn], nb4 = cS[3 * kn + 1], nc4 = cS[3 * kn + 2];
+        const float4 nl = lamS[kn];  // the next contact's impulses (stale only when kn == k)
+        const int r = 3 * k;
+        const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
+        const float gn = wn + ca.z * ln;
+        const float lnn = fmaxf(0.f, ln - gn * ca.y);
+        const float dn = lnn - ln;
+        const float g1 = w1 + cc4.y * dn + cb4.y * l1;
+        const float g2 = w2 + cc4.z * dn + cc4.x * l2;
+        float l1t = l1 - g1 * cb4.x;
+        float l2t = l2 - g2 * cb4.w;
+        const float lim = P.mu * lnn;
+        const float nt2 = l1t * l1t + l2t * l2t;
+        const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+        l1t *= sc;
+        l2t *= sc;
+        w += an * dn + a1 * (l1t - l1) + a2 * (l2t - l2);
+        lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
+        const bool same = kn == k;
+        ln = same ? lnn : nl.x;
+        l1 = same ? l1t : nl.y;
+        l2 = same ? l2t : nl.z;
+        an = nan0; a1 = na1; a2 = na2;
+        ca = na; cb4 = nb4; cc4 = nc4;
+        k = kn;
+      }
+      __syncwarp();
       // u = sum_r Y_r lam_r (lane = dof)
-      for (int r = 0; r < 3 * nc; ++r) u += shf(lam, r) * Yg[(size_t)r * 32 + lane];
-#pragma unroll
-      for (int t = 0; t < 3; ++t) lam_a[t] = shf(lam, (3 * lane + t) & 31);
+      for (int kk = 0; kk < nc; ++kk) {
+        const float4 l4 = lamS[kk];
+        const float* Yk = Yg + (size_t)(3 * kk) * 32 + lane;
+        u += l4.x * Yk[0] + l4.y * Yk[32] + l4.z * Yk[64];
+      }
+      if (lane < nc) {
+        const float4 l4 = lamS[lane];
+        lam_a[0] = l4.x; lam_a[1] = l4.y; lam_a[2] = l4.z;
+      }
     } else if (nc > 0) {
-      // dof space (lane = dof, u = L^T (v - v_free)); the impulses of contact
-      // k live in lane k & 31 (slot k >> 5)
+      // Dof space (lane = dof, u = L^T (v - v_free)), one contact of
+      // lookahead: the next contact's row products are reduced over the warp
+      // from u before the current update lands, then brought up to date with
+      // B_k (u changes by Y_k^T dlam_k), so that the five-level reduction
+      // runs beside the update instead of ahead of it.  Contact impulses sit
+      // in shared memory: every lane computes and stores them alike and reads
+      // back its own writes.
+      float4* lamS = reinterpret_cast<float4*>(&sm.R[0][0]);
+      for (int k0 = lane; k0 < nc; k0 += 32) lamS[k0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
       const float4* c4 = reinterpret_cast<const float4*>(cstg);
+      int k = 0, kn = nc > 1 ? 1 : 0;
       float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
+      const float* Zn = Yg + (size_t)(3 * kn) * 32;
+      float z0 = Zn[lane], z1 = Zn[32 + lane], z2 = Zn[64 + lane];
       float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
-      for (int it = 0; it < P.iters; ++it) {
-        for (int k = 0; k < nc; ++k) {
-          // prefetch the next contact's rows and constants
-          const int kn = (k + 1 < nc) ? k + 1 : 0;
-          const float* Yn = Yg + (size_t)(3 * kn) * 32;
-          const float ny0 = Yn[lane], ny1 = Yn[32 + lane], ny2 = Yn[64 + lane];
-          const float4 na = c4[3 * kn], nb4 = c4[3 * kn + 1], nc4 = c4[3 * kn + 2];
-          float s0 = y0 * u, s1 = y1 * u, s2 = y2 * u;
-          warp_sum3(s0, s1, s2, lane);
-          const int src = k & 31;
-          const bool hi = k >= 32;
-          const float ln = shf(hi ? lam_b[0] : lam_a[0], src);
-          const float l1 = shf(hi ? lam_b[1] : lam_a[1], src);
-          const float l2 = shf(hi ? lam_b[2] : lam_a[2], src);
-          // constants: (b_n, inv_n, R_n, b_t1), (inv_t1, R_t1, b_t2, inv_t2), (R_t2, A_t1n, A_t2n, 0)
-          const float gn = s0 + ca.x + ca.z * ln;
-          const float lnn = fmaxf(0.f, ln - gn * ca.y);
-          const float dn = lnn - ln;
-          const float g1 = s1 + cc4.y * dn + ca.w + cb4.y * l1;
-          const float g2 = s2 + cc4.z * dn + cb4.z + cc4.x * l2;
-          float l1t = l1 - g1 * cb4.x;
-          float l2t = l2 - g2 * cb4.w;
-          const float lim = P.mu * lnn;
-          const float nt2 = l1t * l1t + l2t * l2t;
-          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
-          l1t *= sc;
-          l2t *= sc;
-          u += y0 * dn + y1 * (l1t - l1) + y2 * (l2t - l2);
-          const bool mine_a = lane == src && !hi, mine_b = lane == src && hi;
-          lam_a[0] = mine_a ? lnn : lam_a[0];
-          lam_a[1] = mine_a ? l1t : lam_a[1];
-          lam_a[2] = mine_a ? l2t : lam_a[2];
-          lam_b[0] = mine_b ? lnn : lam_b[0];
-          lam_b[1] = mine_b ? l1t : lam_b[1];
-          lam_b[2] = mine_b ? l2t : lam_b[2];
-          y0 = ny0; y1 = ny1; y2 = ny2;
-          ca = na; cb4 = nb4; cc4 = nc4;
-        }
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // Y_k . u before update k (u = 0 at the start)
+      float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of contact k
+      const int nupd = P.iters * nc;
+      for (int upd = 0; upd < nupd; ++upd) {
+        const int knn = (kn + 1 < nc) ? kn + 1 : 0;
+        const float* Zz = Yg + (size_t)(3 * knn) * 32;
+        const float zz0 = Zz[lane], zz1 = Zz[32 + lane], zz2 = Zz[64 + lane];
+        const float4 na = c4[6 * kn], nb4 = c4[6 * kn + 1], nc4 = c4[6 * kn + 2];
+        const float4 bq0 = c4[6 * k + 3], bq1 = c4[6 * k + 4], bq2 = c4[6 * k + 5];
+        const float4 nl = lamS[kn];  // stale only when kn == k
+        // the next contact's row products against u before this update
+        float p0 = z0 * u, p1 = z1 * u, p2 = z2 * u;
+        warp_sum3(p0, p1, p2, lane);
+        // constants: (b_n, inv_n, R_n, b_t1), (inv_t1, R_t1, b_t2, inv_t2), (R_t2, A_t1n, A_t2n, 0)
+        const float gn = s0 + ca.x + ca.z * ln;
+        const float lnn = fmaxf(0.f, ln - gn * ca.y);
+        const float dn = lnn - ln;
+        const float g1 = s1 + cc4.y * dn + ca.w + cb4.y * l1;
+        const float g2 = s2 + cc4.z * dn + cb4.z + cc4.x * l2;
+        float l1t = l1 - g1 * cb4.x;
+        float l2t = l2 - g2 * cb4.w;
+        const float lim = P.mu * lnn;
+        const float nt2 = l1t * l1t + l2t * l2t;
+        const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+        l1t *= sc;
+        l2t *= sc;
+        const float d1 = l1t - l1, d2 = l2t - l2;
+        u += y0 * dn + y1 * d1 + y2 * d2;
+        lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
+        // B_k row-major in bq0..bq2: (b00 b01 b02 b10) (b11 b12 b20 b21) (b22 ...)
+        s0 = p0 + bq0.x * dn + bq0.y * d1 + bq0.z * d2;
+        s1 = p1 + bq0.w * dn + bq1.x * d1 + bq1.y * d2;
+        s2 = p2 + bq1.z * dn + bq1.w * d1 + bq2.x * d2;
+        const bool same = kn == k;
+        ln = same ? lnn : nl.x;
+        l1 = same ? l1t : nl.y;
+        l2 = same ? l2t : nl.z;
+        y0 = z0; y1 = z1; y2 = z2;
+        z0 = zz0; z1 = zz1; z2 = zz2;
+        ca = na; cb4 = nb4; cc4 = nc4;
+        k = kn;
+        kn = knn;
+      }
+      __syncwarp();
+      {
+        const float4 la = lane < nc ? lamS[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 lb = lane + 32 < nc ? lamS[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+        lam_a[0] = la.x; lam_a[1] = la.y; lam_a[2] = la.z;
+        lam_b[0] = lb.x; lam_b[1] = lb.y; lam_b[2] = lb.z;
       }
     }
     float vplus = vfree + upper_solve(sm, u, nv, lane);
