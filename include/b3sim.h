@@ -249,27 +249,36 @@ int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
 
 /* ---- Stepping without any allocation --------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
- * cannot allocate device memory at the moment they step: code running while a
- * CUDA graph is being captured (an allocation is not a capturable operation),
- * hosts whose device memory is owned by another allocator or fixed up front
- * (game engines, embedded controllers, plugins inside a larger GPU
- * application), and real-time loops that must not block in the driver.
+ * cannot allocate device memory when they step: hosts whose device memory is
+ * owned by another allocator or fixed up front (game engines, embedded
+ * controllers, plugins inside a larger GPU application, where a cudaMalloc
+ * would bypass the host's accounting or fail against its budget), and
+ * real-time loops that must not block in the driver (cudaMalloc and cudaFree
+ * may synchronise the device).
  *
  * sim_step_n_noalloc advances n variants that the CALLER keeps in device
- * memory it already owns, using the same step kernel as sim_step_n.  It calls
- * no cudaMalloc, cudaFree or allocating library routine.  Its per-variant
- * scratch (contact candidates, narrow-phase staging rows, contact
- * Jacobian rows and Gauss-Seidel constants, about 45 KB per variant) is a fixed array inside this library: SIM_NOALLOC_MAX_VARIANTS
- * variants, about 2.9 MB, held by every device that loads the library until
+ * memory it already owns.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Its per-variant scratch (contact candidates, narrow-phase
+ * staging rows, contact Jacobian rows and Gauss-Seidel constants, about 48 KB
+ * per variant) is a fixed array inside this library: SIM_NOALLOC_MAX_VARIANTS
+ * variants, about 3.1 MB, held by every device that loads the library until
  * the process exits.  Larger n is rejected with SIM_EINVAL.
  *   - cfg->device is made current; cfg->stream (0: the legacy default
  *     stream) receives the work, asynchronously.
- *   - The first call on a device looks up the scratch's device address; make
- *     that first call before any stream capture on that device.
+ *   - The first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture
+ *     on that device.
  *   - All calls share the one scratch array, which keeps the last call's
  *     contents; calls whose work overlaps on the GPU (other streams, other
  *     host threads) race on it and must be serialised by the caller.
- *   - Variants are stepped in the order given (no size sorting).
+ *   - Every variant is stepped by the general warp-per-robot step kernel of
+ *     sim_step_n, in the order given (no size sorting).  Variants that are a
+ *     single free body take that general kernel here too, not the
+ *     one-thread-per-body kernel sim_step_n uses for them, so their results
+ *     differ from sim_step_n's by FP32 rounding (about 1e-5 m over 200 steps
+ *     of a tumbling cube).
+ *   - Failures are reported per host thread: sim_last_error(NULL) returns the
+ *     message of the calling thread's last failed call.
  * Device layout expected in *pop (all device pointers, caller-owned):
  *   model_f  n x SIM_MODEL_NF x 32 floats, [variant][field][body slot]:
  *            joint frame R (9, row-major), joint frame p (3), half size (3),
@@ -283,7 +292,8 @@ int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
  *            from body 0 to this body, both ends included), child mask, depth
  *            (body 0: 0).
  *   meta     n x 4 int32: n_bodies, maximum depth, pair count, offset of the
- *            variant's pairs in `pairs`.
+ *            variant's pairs in `pairs`; the buffer must be 16-byte aligned
+ *            (each row is read as one vector), else SIM_EINVAL.
  *   pairs    uint16 (a << 8) | b for every body pair a < b that may collide
  *            (b's parent is not a, and neither excludes the other).
  *   q, v, cpg, status  state rows with strides 32, 32, 64 floats and one
@@ -309,7 +319,8 @@ typedef struct {
 int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, int32_t n_steps);
 
 /* Human-readable description of the last failure on this context ("" if
- * none).  ctx may be NULL for a failure in sim_create. */
+ * none).  ctx may be NULL for a failure in sim_create or
+ * sim_step_n_noalloc: that message is kept per host thread. */
 const char* sim_last_error(const sim_ctx_t* ctx);
 
 #ifdef __cplusplus

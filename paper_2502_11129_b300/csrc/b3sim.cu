@@ -73,8 +73,10 @@ struct sim_ctx {
 
 namespace {
 
-const char* g_create_error = "";
-std::string g_create_error_buf;
+// errors of calls without a context (sim_create, sim_step_n_noalloc), one
+// slot per host thread: sim_last_error(NULL) reads the calling thread's own
+thread_local const char* g_create_error = "";
+thread_local std::string g_create_error_buf;
 
 int fail(sim_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -542,6 +544,11 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
   if (!pop->model_f || !pop->model_i || !pop->meta || !pop->pairs || !pop->q || !pop->v || !pop->cpg ||
       !pop->status) {
     g_create_error = "sim_step_n_noalloc: a device pointer is NULL";
+    return SIM_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(pop->meta) & 15u) {
+    // the step kernel reads each variant's meta row as one 16-byte vector
+    g_create_error = "sim_step_n_noalloc: meta must be 16-byte aligned";
     return SIM_EINVAL;
   }
   if (cfg->device < 0 || cfg->device >= kMaxDevices) {

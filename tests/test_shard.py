@@ -44,9 +44,22 @@ def test_equal_costs_split_evenly_and_bad_input_is_rejected():
         SH.balanced_shards([1.0], 0)
 
 
-def fake_fitness(pop):
-    # a deterministic per-robot value built from the genome alone
-    return pop.nb * 0.01 + pop.w_int.sum(axis=1)
+STEPS = 100
+
+
+def engine_fitness(pop):
+    """Fitness after STEPS steps from the population's start, simulated by the
+    host engine (libb3cpu): the real simulator a rank would run on its shard."""
+    from paper_2502_11129_b300 import cpu as CP
+    from paper_2502_11129_b300 import sim as S
+    Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+    cs = CP.CpuSim(threads=1)
+    cs.set_population(pop)
+    cs.set_state(Q, V, Sx)
+    cs.step(STEPS)
+    f = cs.fitness()
+    cs.close()
+    return f
 
 
 def _worker(rank, world, port, out_dir):
@@ -54,12 +67,12 @@ def _worker(rank, world, port, out_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    pop = P.grammar(37, seed=11)
+    pop = P.grammar(37, seed=11).as_float32()
     seen = []
 
     def sim(sub):
         seen.append(sub.n)
-        return fake_fitness(sub)
+        return engine_fitness(sub)
 
     f = SH.run_sharded(pop, sim, dist)
     np.save(os.path.join(out_dir, f"r{rank}.npy"), np.concatenate([[seen[0]], f]))
@@ -75,9 +88,13 @@ def _free_port():
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_run_sharded_gathers_every_result_on_every_rank(tmp_path, world):
+    """Every rank simulates its shard with the host engine for 100 steps; the
+    gathered fitness equals, bitwise and on every rank, one process
+    simulating the whole population (robots are independent)."""
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
-    pop = P.grammar(37, seed=11)
-    ref = fake_fitness(pop)
+    pop = P.grammar(37, seed=11).as_float32()
+    ref = engine_fitness(pop).astype(np.float64)
+    assert np.abs(ref).max() > 0  # the robots moved
     sizes = []
     for r in range(world):
         a = np.load(tmp_path / f"r{r}.npy")
@@ -87,6 +104,6 @@ def test_run_sharded_gathers_every_result_on_every_rank(tmp_path, world):
 
 
 def test_single_rank_runs_everything_locally():
-    pop = P.grammar(5, seed=2)
-    f = SH.run_sharded(pop, fake_fitness, None)
-    assert np.array_equal(f, fake_fitness(pop))
+    pop = P.grammar(5, seed=2).as_float32()
+    f = SH.run_sharded(pop, engine_fitness, None)
+    assert np.array_equal(f, engine_fitness(pop))

@@ -1,11 +1,12 @@
 """Allocation-free stepping against the context-based entry point.
 
 sim_step_n_noalloc exists for callers that cannot allocate device memory when
-they step: code that runs while a CUDA graph is being captured (an allocation
-cannot be captured), hosts whose device memory is owned by another allocator
-or fixed up front, and real-time loops that must not block in the driver.
-They keep the population in device buffers they already own; the library's
-per-variant scratch comes from a fixed array inside the library.
+they step: hosts whose device memory is owned by another allocator or fixed up
+front (a cudaMalloc would bypass their accounting or fail against their
+budget), and real-time loops that must not block in the driver (cudaMalloc and
+cudaFree may synchronise the device).  They keep the population in device
+buffers they already own; the library's per-variant scratch comes from a fixed
+array inside the library.
 
 This test packs a population in the documented device layout (include/b3sim.h),
 steps it twice in a row through sim_step_n_noalloc, and compares both results
@@ -104,6 +105,19 @@ def rel_err(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1.0)
 
 
+def _device_pop(pop, Q, V, Sx):
+    import torch
+    dev = torch.device("cuda", 0)
+    mf, mi, meta, pairs = pack(pop)
+    t = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for k, a in
+         dict(mf=mf, mi=mi, meta=meta, pairs=pairs.view(np.int16), q=Q, v=V, s=Sx).items()}
+    t["st"] = torch.zeros(pop.n, dtype=torch.int32, device=dev)
+    dp = S.DevicePopulation(pop.n, t["mf"].data_ptr(), t["mi"].data_ptr(), t["meta"].data_ptr(),
+                            t["pairs"].data_ptr(), t["q"].data_ptr(), t["v"].data_ptr(), t["s"].data_ptr(),
+                            t["st"].data_ptr())
+    return t, dp
+
+
 def test_noalloc_matches_context_entry_on_two_calls():
     import torch
 
@@ -117,13 +131,7 @@ def test_noalloc_matches_context_entry_on_two_calls():
     ref.set_state(Q, V, Sx)
 
     dev = torch.device("cuda", 0)
-    mf, mi, meta, pairs = pack(pop)
-    t = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for k, a in
-         dict(mf=mf, mi=mi, meta=meta, pairs=pairs.view(np.int16), q=Q, v=V, s=Sx).items()}
-    t["st"] = torch.zeros(pop.n, dtype=torch.int32, device=dev)
-    dp = S.DevicePopulation(pop.n, t["mf"].data_ptr(), t["mi"].data_ptr(), t["meta"].data_ptr(),
-                            t["pairs"].data_ptr(), t["q"].data_ptr(), t["v"].data_ptr(), t["s"].data_ptr(),
-                            t["st"].data_ptr())
+    t, dp = _device_pop(pop, Q, V, Sx)
     cfg = config(stream=0)
     L = S.lib()
     for call in range(2):
@@ -142,12 +150,52 @@ def test_noalloc_matches_context_entry_on_two_calls():
     ref.close()
 
 
+def test_noalloc_single_free_bodies_take_the_general_kernel():
+    """Free cubes: sim_step_n steps them one thread per body, this entry point
+    with the general warp kernel; the two agree to FP32 rounding (the bar of
+    the CPU engine's one-body / general-step comparison), on two calls."""
+    import torch
+
+    pop = P.boxes(24, seed=13, vel_sigma=2.0).as_float32()
+    q = pop.q0.copy()
+    q[:, 2] = np.random.default_rng(14).uniform(0.02, 0.3, pop.n)
+    Q, V, Sx = S.state_rows(pop, q, pop.v0, np.zeros((pop.n, 64)))
+    ref = S.Sim()
+    ref.set_population(pop)
+    ref.set_state(Q, V, Sx)
+    dev = torch.device("cuda", 0)
+    t, dp = _device_pop(pop, Q, V, Sx)
+    cfg = config(stream=0)
+    L = S.lib()
+    for call in range(2):
+        assert L.sim_step_n_noalloc(C.byref(cfg), C.byref(dp), 100) == 0, L.sim_last_error(None)
+        torch.cuda.synchronize(dev)
+        ref.step(100)
+        rq, rv, _, rst = ref.read_state()
+        gq, gv = t["q"].cpu().numpy(), t["v"].cpu().numpy()
+        gst = t["st"].cpu().numpy().view(np.uint32)
+        assert np.array_equal(gst, rst) and (gst & 5).sum() == 0, call
+        assert np.abs(gq[:, :7] - rq[:, :7]).max() < 5e-5, call
+        assert np.abs(gv[:, :6] - rv[:, :6]).max() < 1e-4 * max(1.0, np.abs(rv[:, :6]).max()), call
+    ref.close()
+
+
 def test_noalloc_rejects_more_variants_than_its_scratch():
     L = S.lib()
-    dp = S.DevicePopulation(S_MAX + 1, 1, 1, 1, 1, 1, 1, 1, 1)
+    dp = S.DevicePopulation(S_MAX + 1, 16, 16, 16, 16, 16, 16, 16, 16)
     cfg = config()
     assert L.sim_step_n_noalloc(C.byref(cfg), C.byref(dp), 1) == -1
     assert b"64" in L.sim_last_error(None)
+
+
+def test_noalloc_rejects_a_misaligned_meta_buffer():
+    """The meta rows are read as 16-byte vectors: a buffer at a 4-byte offset
+    is refused on the host, before anything is launched."""
+    L = S.lib()
+    dp = S.DevicePopulation(4, 256, 256, 256 + 4, 256, 256, 256, 256, 256)
+    cfg = config()
+    assert L.sim_step_n_noalloc(C.byref(cfg), C.byref(dp), 1) == -1
+    assert b"aligned" in L.sim_last_error(None)
 
 
 S_MAX = 64
