@@ -372,6 +372,50 @@ def test_box_box_edge_edge_crossed():
     assert np.allclose(p, [ca[0], cb[1], top_a - d / 2], atol=1e-12)
 
 
+def _two_boxes(pa, Ra, ha, pb, Rb, hb):
+    """Fixed root far away with two boxes of any half sizes as its children."""
+    bodies = [dict(half=(0.05, 0.05, 0.05), mass=1.0),
+              dict(parent=0, axis=1, R_fix=Ra, p_fix=pa, half=tuple(ha)),
+              dict(parent=0, axis=1, R_fix=Rb, p_fix=pb, half=tuple(hb))]
+    return H.make_model(bodies, root_fixed=True, root_p=(0.0, 0.0, 5.0))
+
+
+@pytest.mark.parametrize("ratio,face", [(0.93, False), (0.97, True)])
+def test_box_box_face_preferred_unless_edge_below_095(ratio, face):
+    """The separating-axis choice prefers a face axis unless the best edge
+    axis overlaps less than 0.95 x the best face axis.  A plate A (half sizes
+    a = (0.01, 0.03, 0.05)) turned 45 deg about y and a cube B (b = 0.03)
+    turned 45 deg about x, B straight above A by dz: A's top edge (along y)
+    and B's bottom edge (along x) cross, and by the support functions
+      edge axis z:      e = (a1 + a3 + b2 + b3)/sqrt2 - dz,
+      face axis A_x:    f = a1 + b1/sqrt2 + (b2 + b3)/2 - dz/sqrt2,
+    the smallest edge and face overlaps (every other axis overlaps by more
+    than 2 cm).  dz is solved for e = ratio * f; the edge overlap is the
+    smaller of the two in both cases.  Below 0.95 the pair gives the
+    edge-edge point (one contact, normal -z, depth e); above it the face case
+    (normal A_x from B to A, deepest point exactly f)."""
+    c = np.sqrt(0.5)
+    a = np.array([0.01, 0.03, 0.05])
+    b = np.array([0.03, 0.03, 0.03])
+    K = (a[0] + a[2] + b[1] + b[2]) * c
+    F0 = a[0] + c * b[0] + (b[1] + b[2]) / 2
+    dz = (K - ratio * F0) / (1 - ratio * c)
+    e, f = K - dz, F0 - c * dz
+    assert e < f and abs(e / f - ratio) < 1e-12
+    Ra, Rb = H.rot("y", np.pi / 4), H.rot("x", np.pi / 4)
+    ca = np.array([0.0, 1.0, 0.0])
+    m = _two_boxes(ca, Ra, a, ca + np.array([0.0, 0.0, dz]), Rb, b)
+    cl = O.contacts(m, np.zeros(2), O.default_params(ground=0))
+    if face:
+        assert len(cl["a"]) >= 1
+        assert np.allclose(cl["n"], [Ra[:, 0]] * len(cl["a"]), atol=1e-12)
+        assert abs(cl["depth"].max() - f) < 1e-12
+    else:
+        assert len(cl["a"]) == 1
+        assert np.allclose(cl["n"][0], [0.0, 0.0, -1.0], atol=1e-12)
+        assert abs(cl["depth"][0] - e) < 1e-12
+
+
 def test_box_box_separation_agrees_with_point_sampling():
     """SAT verdicts against Monte-Carlo: a separated pair has no sample point
     inside both boxes; a pair reported 5 mm deep has some."""

@@ -82,6 +82,48 @@ def test_adam_first_step_is_lr_times_sign():
     assert np.allclose(m2["a"], 0.1 * g["a"]) and np.allclose(v2["a"], 0.001 * g["a"] ** 2)
 
 
+def test_adam_constant_gradient_steps_lr_at_every_t():
+    """Kingma & Ba 2015: with m = v = 0 at the start and a constant gradient g,
+    m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so the bias-corrected moments
+    are exactly g and g^2 and every step is lr * g / (|g| + eps); a wrong
+    exponent in either correction breaks this at t = 2 and t = 3."""
+    g = dict(a=np.array([0.3, -0.01, 2.0, -7.5]))
+    p = dict(a=np.array([1.0, -2.0, 0.5, 0.0]))
+    m = dict(a=np.zeros(4))
+    v = dict(a=np.zeros(4))
+    lr = 0.01
+    step = lr * g["a"] / (np.abs(g["a"]) + 1e-8)
+    for t in (1, 2, 3):
+        p2, m, v = M.adam_step(p, g, m, v, t, lr=lr)
+        assert np.allclose(p2["a"] - p["a"], -step, rtol=1e-12, atol=1e-15), t
+        assert np.allclose(m["a"], (1 - 0.9 ** t) * g["a"], rtol=1e-12), t
+        assert np.allclose(v["a"], (1 - 0.999 ** t) * g["a"] ** 2, rtol=1e-12), t
+        p = p2
+
+
+def test_adam_corrected_moments_are_normalised_weighted_means():
+    """The bias-corrected first moment after t steps is the mean of the
+    gradients seen so far weighted by b1^(t - i), normalised to sum 1 (the
+    weights (1 - b1) b1^(t - i) sum to 1 - b1^t); the second moment likewise
+    with b2 and g^2.  Checked through the parameter path of steps 1, 2, 3 with
+    changing gradients."""
+    b1, b2, eps, lr = 0.9, 0.999, 1e-8, 0.05
+    gs = [np.array([1.0, -3.0]), np.array([2.0, 0.5]), np.array([4.0, -1.0])]
+    p = dict(a=np.array([0.2, 0.7]))
+    m = dict(a=np.zeros(2))
+    v = dict(a=np.zeros(2))
+    x = p["a"].copy()
+    for t in (1, 2, 3):
+        p, m, v = M.adam_step(p, dict(a=gs[t - 1]), m, v, t, lr=lr)
+        w1 = np.array([b1 ** (t - i) for i in range(1, t + 1)])
+        w2 = np.array([b2 ** (t - i) for i in range(1, t + 1)])
+        G = np.array(gs[:t])
+        mh = (w1[:, None] * G).sum(axis=0) / w1.sum()
+        vh = (w2[:, None] * G ** 2).sum(axis=0) / w2.sum()
+        x = x - lr * mh / (np.sqrt(vh) + eps)
+        assert np.allclose(p["a"], x, rtol=1e-12, atol=1e-15), t
+
+
 def test_encoding_of_a_hand_built_quadruped():
     pop = P.quadrupeds(1)
     x = M.encode_population(pop)[0]
