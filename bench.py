@@ -16,10 +16,13 @@ Printed JSON (rank 0):
   e2e      the same metric through the C ABI with pinned host buffers:
            host->device state upload, the steps, device->host state read per
            bench step;
-  roofline step kernel vs the FP32 ALU peak (148 SMs x 128 lanes x 2 flop x
-           max SM clock); algorithmic flops per variant-step counted by the
-           FP64 oracle on a sample of the same workload (contact-dependent
-           phases scaled to the GPU's own contact count);
+  roofline step kernel vs the FP32 ALU peak measured on the same GPU by the
+           library's FFMA-loop kernel (scaled to the SM clock of the timed
+           steps); algorithmic flops per variant-step counted by the FP64
+           oracle on a sample of the same workload (contact-dependent phases
+           scaled to the GPU's own contact count);
+  surrogate  the learned part at the screening sizes: training time per
+           epoch over 50000 pairs, predict + top-k of 65536 offspring;
   cpu_baseline  the FP64 oracle on the host cores, on a sample (every 16th
            robot, 2000 steps).
 --impl reference times that oracle alone (bounded sample per bench step).
@@ -184,6 +187,22 @@ def oracle_sample(pop, steps, threads):
     return vs / dt, d, dt
 
 
+def surrogate_record(device):
+    """The learned half of the headline metric at the screening sizes (a
+    128 -> 256 -> 256 -> 1 BF16 MLP, every dense layer on tcgen05): training
+    time per epoch over 50000 (genotype, displacement) pairs, predicting and
+    ranking 65536 offspring (top 4096), each call with its host copies."""
+    from paper_2502_11129_b300 import surrogate as SG
+    t = SG.timing(n_train=50000, n_screen=65536, k=4096, epochs=3, batch=1024, seed=0)
+    return {"train_pairs": 50000, "train_s_per_epoch": t["train_s"] / t["train_epochs"],
+            "train_tflops_incl_host": t["train_tflops_incl_host"],
+            "screen_n": 65536, "screen_topk": 4096, "predict_s": t["predict_s"], "topk_s": t["topk_s"],
+            "screen_per_s": 65536 / (t["predict_s"] + t["topk_s"]),
+            "predict_tflops_incl_host": t["predict_tflops_incl_host"],
+            "note": "wall time of each C-ABI call, host<->device copies included; encode of 2048 robots "
+                    f"{t['encode_2048_s'] * 1e3:.2f} ms"}
+
+
 def run_ours(args, world, rank, local, dist):
     import torch
     from paper_2502_11129_b300 import population as P
@@ -295,15 +314,34 @@ def run_ours(args, world, rank, local, dist):
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count
         max_mhz = (clk or {}).get("sm_max_mhz") or 2032.0
-        peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        nominal = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
         units_per_launch = args.variants * spl
         achieved = fl_per_vs * units_per_launch / launch_s / 1e12
+        # measured FP32 peak: the library's FFMA-loop kernel, clocks sampled
+        # while it runs, scaled to the SM clock sampled during the timed steps
+        fclk = Clocks(local)
+        fclk.start()
+        pk = S.fp32_peak(local, 25)
+        fc = fclk.stop() or {}
+        bench_mhz = (clk or {}).get("sm_mhz")
+        ffma_mhz = fc.get("sm_mhz")
+        scale = bench_mhz / ffma_mhz if bench_mhz and ffma_mhz else 1.0
+        peak = pk["tflops"] * scale
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak, "traffic": ncu_traffic(),
                            "flops_per_unit": fl_per_vs, "unit_name": "variant-step",
                            "units_per_launch": units_per_launch, "launch_ms": launch_s * 1e3,
-                           "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                           "peak_basis": "measured",
+                           "peak_measurement": {
+                               "kernel": "FFMA loop (sim_fp32_peak: 8 independent chains a thread, 64 warps per SM)",
+                               "tflops": pk["tflops"], "ms": pk["ms"], "sm_mhz": ffma_mhz,
+                               "reasons": fc.get("reasons"), "scaled_to_bench_sm_mhz": bench_mhz,
+                               "flops_per_sm_cycle": (pk["tflops"] * 1e12 / (sms * ffma_mhz * 1e6)
+                                                      if ffma_mhz else None)},
+                           "peak_nominal": nominal,
+                           "nominal_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
                            "oracle_contacts_per_variant_step": c_o}
+        out["surrogate"] = surrogate_record(local)
     sm.close()
     return out
 

@@ -318,6 +318,18 @@ typedef struct {
 
 int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, int32_t n_steps);
 
+/* ---- FP32 peak of the device (measurement; no counterpart in the paper) ----
+ * The step kernel runs on the FP32 FMA pipe (no dense contraction in the
+ * step), so its roofline denominator is what that pipe delivers: this call
+ * launches `launches` back-to-back kernels of independent FFMA chains (every
+ * resident thread of every SM, 8 chains a thread, 64 warps per SM) on a
+ * private stream of `device` and returns their FLOP count (an FMA is 2) and
+ * device time in milliseconds (CUDA events around all launches), plus the SM
+ * count.  About 40 ms per launch.  Synchronises; returns SIM_OK, SIM_EINVAL
+ * (launches < 1 or NULL outputs; sim_last_error(NULL) says which) or
+ * SIM_ECUDA. */
+int sim_fp32_peak(int32_t device, int32_t launches, double* flops, float* ms, int32_t* sm_count);
+
 /* Human-readable description of the last failure on this context ("" if
  * none).  ctx may be NULL for a failure in sim_create or
  * sim_step_n_noalloc: that message is kept per host thread. */

@@ -498,6 +498,33 @@ cudaError_t noalloc_setup(int dev, NoallocAddrs* out) {
   return cudaSuccess;
 }
 
+// FP32 FMA throughput: independent chains x_k <- x_k a + b (a < 1, so the
+// values settle at b / (1 - a) and stay finite), 8 per thread, unrolled 16
+// times per loop trip; the final sum is stored only if it takes a value it
+// cannot take, which keeps every chain live without memory traffic.
+constexpr int kFfmaThreads = 256;
+constexpr int kFfmaBlocksPerSm = 8;  // 64 resident warps per SM
+constexpr int kFfmaChains = 8;
+constexpr int kFfmaUnroll = 16;
+constexpr int kFfmaPerIter = kFfmaChains * kFfmaUnroll;
+
+__global__ void __launch_bounds__(kFfmaThreads) ffma_loop(float* out, float a, float b, int iters) {
+  float x[kFfmaChains];
+#pragma unroll
+  for (int k = 0; k < kFfmaChains; ++k) x[k] = 1e-3f * (float)threadIdx.x + (float)k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kFfmaUnroll; ++u) {
+#pragma unroll
+      for (int k = 0; k < kFfmaChains; ++k) x[k] = fmaf(x[k], a, b);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kFfmaChains; ++k) s += x[k];
+  if (s == -1.f) out[blockIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1011,6 +1038,51 @@ int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int
   for (int k = 0; k < nc; ++k)
     for (int t = 0; t < 3; ++t) lambda[3 * k + t] = buf[32 + 4 * k + t];
   *n_out = nc;
+  return SIM_OK;
+}
+
+int sim_fp32_peak(int32_t device, int32_t launches, double* flops, float* ms, int32_t* sm_count) {
+  if (launches < 1 || !flops || !ms || !sm_count) {
+    g_create_error = "sim_fp32_peak: launches < 1 or a NULL output";
+    return SIM_EINVAL;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float* out = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float) * (size_t)sms * kFfmaBlocksPerSm);
+  const int grid = sms * kFfmaBlocksPerSm;
+  const int iters = 40000;
+  if (e == cudaSuccess) {
+    ffma_loop<<<grid, kFfmaThreads, 0, st>>>(out, 0.9999f, 1e-4f, 100);  // warm-up
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int l = 0; l < launches && e == cudaSuccess; ++l) {
+    ffma_loop<<<grid, kFfmaThreads, 0, st>>>(out, 0.9999f, 1e-4f, iters);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess) {
+    g_create_error_buf = std::string("sim_fp32_peak: ") + cudaGetErrorString(e);
+    g_create_error = g_create_error_buf.c_str();
+    return SIM_ECUDA;
+  }
+  *flops = (double)launches * grid * kFfmaThreads * (double)iters * kFfmaPerIter * 2.0;
+  *ms = t;
+  *sm_count = sms;
   return SIM_OK;
 }
 

@@ -26,7 +26,7 @@ STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: 
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_population", "sim_set_state", "sim_step_n",
            "sim_read_state", "sim_fitness", "sim_autotune", "sim_counters_read",
            "sim_debug_contacts", "sim_debug_solver", "sim_debug_sincos", "sim_robot_cost", "sim_launch_shape", "sim_step_n_noalloc", "sim_set_state_dev", "sim_read_state_dev",
-           "sim_fitness_dev", "sim_stream", "sim_last_error"]
+           "sim_fitness_dev", "sim_stream", "sim_fp32_peak", "sim_last_error"]
 
 
 class SimConfig(C.Structure):
@@ -104,6 +104,8 @@ def lib():
         L.sim_read_state_dev.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp]
         L.sim_fitness_dev.argtypes = [vp, vp, C.c_int32]
         L.sim_stream.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.sim_fp32_peak.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float),
+                                    C.POINTER(C.c_int32)]
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = C.c_char_p
         _lib = L
@@ -314,6 +316,16 @@ class Sim:
                     "sim_debug_solver")
         return dict(vfree=vfree, lam=lam[:3 * n.value].reshape(-1, 3), n=n.value,
                     cycles_per_step=float(cyc[0]), phase_cycles=cyc[1:10].copy())
+
+
+def fp32_peak(device: int = 0, launches: int = 25) -> dict:
+    """FP32 FMA throughput of the device measured by the library's FFMA-loop
+    kernel: FLOP count, device milliseconds, TFLOP/s and SM count."""
+    fl, ms, sms = C.c_double(), C.c_float(), C.c_int32()
+    rc = lib().sim_fp32_peak(device, launches, C.byref(fl), C.byref(ms), C.byref(sms))
+    if rc != 0:
+        raise SimError(f"sim_fp32_peak: {STATUS.get(rc, rc)}: {lib().sim_last_error(None).decode()}")
+    return dict(flops=fl.value, ms=ms.value, tflops=fl.value / (ms.value * 1e-3) / 1e12, sms=sms.value)
 
 
 def debug_sincos(x):
