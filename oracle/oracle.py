@@ -118,6 +118,11 @@ def lib():
                                       P(C.c_double), P(C.c_int32)]
         L.orc_run.argtypes = [P(Model), P(Params), C.c_int, P(C.c_double), P(C.c_double),
                               P(C.c_double), P(C.c_uint32), P(Stats)]
+        L.orc_contacts_flip.argtypes = [P(Model), P(Params), P(C.c_double), C.c_double, P(C.c_int32), C.c_int32,
+                                        P(ContactList), P(C.c_int32), P(C.c_int32), P(C.c_double)]
+        L.orc_step_flip.argtypes = [P(Model), P(Params), P(C.c_double), P(C.c_double), P(C.c_double),
+                                    P(C.c_uint32), C.c_double, P(C.c_int32), C.c_int32, P(C.c_int32),
+                                    P(C.c_int32), P(C.c_double)]
         L.orc_run_many.argtypes = [P(Model), C.c_int, P(Params), C.c_int, P(C.c_double), C.c_int,
                                    P(C.c_double), C.c_int, P(C.c_double), C.c_int,
                                    P(C.c_uint32), P(Stats), C.c_int]
@@ -258,6 +263,100 @@ def run(m: Model, q, v, s, nsteps: int, prm: Params | None = None, status: int =
     lib().orc_run(C.byref(m), C.byref(prm), int(nsteps), _dp(q), _dp(v), _dp(s),
                   C.byref(st), C.byref(stats))
     return q, v, s, st.value, stats
+
+
+MAXNEAR = 64
+
+
+def step_flip(m: Model, q, v, s, flips=(), band: float = 1e-5, prm: Params | None = None, status: int = 0):
+    """One step with the near-threshold decisions numbered in ``flips`` taken
+    the other way (orc_step_flip).  Returns (q, v, s, status, near, margin):
+    ``near`` are the numbers of the decisions within ``band`` that the step
+    met (at most MAXNEAR listed)."""
+    prm = prm or default_params()
+    q = np.array(q, dtype=np.float64); v = np.array(v, dtype=np.float64)
+    s = np.array(s, dtype=np.float64)
+    if s.size == 0:
+        s = np.zeros(2 * MAXB)
+    st = C.c_uint32(status)
+    fl = np.ascontiguousarray(list(flips), dtype=np.int32)
+    near = np.zeros(MAXNEAR, np.int32)
+    nn = C.c_int32(0)
+    mg = C.c_double(0.0)
+    rc = lib().orc_step_flip(C.byref(m), C.byref(prm), _dp(q), _dp(v), _dp(s), C.byref(st), float(band),
+                             fl.ctypes.data_as(C.POINTER(C.c_int32)) if fl.size else None, int(fl.size),
+                             near.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nn), C.byref(mg))
+    if rc != 0:
+        raise ValueError("orc_step_flip: bad arguments")
+    return q, v, s, st.value, near[:min(nn.value, MAXNEAR)].copy(), mg.value
+
+
+def _contact_dict(cl, st, margin):
+    n = cl.n
+    return dict(a=np.array(cl.a[:n]), b=np.array(cl.b[:n]),
+                p=np.array([list(cl.p[k]) for k in range(n)]).reshape(n, 3),
+                n=np.array([list(cl.nrm[k]) for k in range(n)]).reshape(n, 3),
+                depth=np.array(cl.depth[:n]), status=st, margin=margin)
+
+
+def contact_outcomes(m: Model, q, band: float = 1e-5, prm: Params | None = None, max_runs: int = 512):
+    """Every valid contact list of one configuration: the tree of its
+    decisions within ``band`` of their thresholds (as step_outcomes).
+    Returns (lists, n_near, complete); lists[0] is the plain one."""
+    prm = prm or default_params()
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    outs = []
+    stack = [()]
+    n_near = 0
+    while stack:
+        if len(outs) >= max_runs:
+            return outs, n_near, False
+        S = stack.pop()
+        cl = ContactList()
+        fl = np.ascontiguousarray(S, dtype=np.int32)
+        near = np.zeros(MAXNEAR, np.int32)
+        nn = C.c_int32(0)
+        mg = C.c_double(0.0)
+        st = lib().orc_contacts_flip(C.byref(m), C.byref(prm), _dp(q), float(band),
+                                     fl.ctypes.data_as(C.POINTER(C.c_int32)) if fl.size else None, int(fl.size),
+                                     C.byref(cl), near.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nn),
+                                     C.byref(mg))
+        if st < 0:
+            raise ValueError("orc_contacts_flip: bad arguments")
+        if not S:
+            n_near = min(nn.value, MAXNEAR)
+        outs.append(_contact_dict(cl, st, mg.value))
+        last = S[-1] if S else -1
+        for x in sorted((int(x) for x in near[:min(nn.value, MAXNEAR)] if x > last), reverse=True):
+            stack.append(S + (x,))
+    return outs, n_near, True
+
+
+def step_outcomes(m: Model, q, v, s, band: float = 1e-5, prm: Params | None = None, max_runs: int = 512):
+    """Every valid outcome of one step whose discrete decisions may go either
+    way: the tree of the step's decisions within ``band`` of their
+    thresholds, explored depth first.  A run that reverses the decisions S
+    reports the near decisions it meets, numbered in its own order; those
+    numbered above max(S) sit after every reversed decision, so their numbers
+    mean the same in the run reversing S + (x,), and every combination is
+    reached once.  Returns (outcomes, n_near, complete): outcomes is a list of
+    (q, v, s, status), the plain step first; n_near the plain step's near
+    decisions; complete False if max_runs cut the tree."""
+    outs = []
+    stack = [()]
+    n_near = 0
+    while stack:
+        if len(outs) >= max_runs:
+            return outs, n_near, False
+        S = stack.pop()
+        qa, va, sa, sta, near, _ = step_flip(m, q, v, s, S, band, prm)
+        if not S:
+            n_near = len(near)
+        outs.append((qa, va, sa, sta))
+        last = S[-1] if S else -1
+        for x in sorted((int(x) for x in near if x > last), reverse=True):
+            stack.append(S + (x,))
+    return outs, n_near, True
 
 
 def run_population(pop, q, v, s, nsteps: int, prm: Params | None = None, threads: int = 1,

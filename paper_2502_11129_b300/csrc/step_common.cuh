@@ -19,6 +19,7 @@ constexpr int kCand = 256;      // contact candidates per step
 constexpr int kCandW = 8;       // floats per candidate row
 constexpr int kYRows = 3 * kCapMax;
 constexpr float kAmin = 1e-10f;  // rows with J M^-1 J^T at or below this are frozen
+constexpr float kClipOn = 1e-6f;  // a clipped polygon's vertex this close to a side plane is on it [m]
 constexpr int kCstW = 12;        // Gauss-Seidel constants per contact (floats)
 constexpr int kMaxPairs = kMaxB * (kMaxB - 1) / 2;  // box/box candidate pairs per robot
 
@@ -136,7 +137,8 @@ __host__ __device__ __forceinline__ void put_candidate(float* cand, int n, const
 
 // Box/box narrow phase of one body pair a < b on one lane: separating-axis
 // test over 15 axes (faces of a, faces of b, edge crosses), then face
-// clipping or the edge-edge point.  Up to 8 contact rows go to `out`
+// clipping (Sutherland-Hodgman, a vertex within kClipOn of a side plane
+// counting as on it) or the edge-edge point.  Up to 8 contact rows go to `out`
 // (8 floats each, candidate layout); returns their count.  Axis choice:
 // minimum overlap, ties to the lowest index, a face unless the best edge
 // overlap is below 0.95 x the best face overlap.  Normals point from b to a.
@@ -239,24 +241,30 @@ __host__ __device__ __noinline__ int box_box_lane(const float (*RR)[32], const f
       const float ps = (pl & 1) ? -1.f : 1.f;
       const float u[3] = {Rx[ax][0], Rx[ax][1], Rx[ax][2]};
       const float eh = hR[ax];
+      // side of every vertex: inside (-1), on the plane (0: within
+      // kClipOn of it) or outside (+1); inside and on vertices are kept, and
+      // a crossing point only joins an inside vertex to an outside one, so
+      // an edge lying on the plane is kept whole
       float dist[8];
+      int side[8];
 #pragma unroll 1
       for (int v = 0; v < np; ++v) {
         const float rel[3] = {poly[cur][v][0] - cR[0], poly[cur][v][1] - cR[1], poly[cur][v][2] - cR[2]};
         dist[v] = ps * dot3(rel, u) - eh;
+        side[v] = fabsf(dist[v]) <= kClipOn ? 0 : (dist[v] < 0.f ? -1 : 1);
       }
       int no = 0;
 #pragma unroll 1
       for (int v = 0; v < np; ++v) {
         const int nx = (v + 1) % np;
-        const bool in_v = dist[v] <= 0.f, in_n = dist[nx] <= 0.f;
+        const bool in_v = side[v] <= 0;
         // at most 8 vertices: a convex quad gains at most one per plane;
         // spurious crossings from rounding past 8 are dropped
         if (in_v && no < 8) {
           for (int k = 0; k < 3; ++k) poly[cur ^ 1][no][k] = poly[cur][v][k];
           ++no;
         }
-        if (in_v != in_n && no < 8) {
+        if (side[v] * side[nx] == -1 && no < 8) {
           const float t = dist[v] / (dist[v] - dist[nx]);
           for (int k = 0; k < 3; ++k) poly[cur ^ 1][no][k] = poly[cur][v][k] + t * (poly[cur][nx][k] - poly[cur][v][k]);
           ++no;

@@ -1,11 +1,12 @@
 """Host (CPU) engine (libb3cpu, the CPU side of the hybrid allocation) vs the
 FP64 oracle, and the hybrid allocation logic -- all on the CPU.
 
-Same bars as the GPU path (tests/test_gpu_parity.py): one step from identical
-FP32-rounded states within 1e-5 relative per variant (velocity scaled by
-max(|v+|, |v_free|, 1)), robots with a discrete decision within 1e-5 of its
-threshold in the oracle reported separately; contact-free flight within
-1e-4 m over 200 steps.
+Same bars as the GPU path (tests/parity.py): one step from identical
+FP32-rounded states, every robot against the closest valid outcome of the
+oracle's step, |dx| / max(|x_ref|, 1) within 1e-5 where FP32 arithmetic meets
+that on every robot of the states (the oracle's FP32 build), else no worse
+than that FP32 yardstick; contact-free flight within 1e-4 m over 200 steps
+(or within twice FP32 arithmetic's own drift, where that exceeds 1e-4 m).
 """
 import os
 
@@ -16,8 +17,9 @@ from paper_2502_11129_b300 import cpu as CP
 from paper_2502_11129_b300 import hybrid as H
 from paper_2502_11129_b300 import population as P
 from paper_2502_11129_b300 import sim as S
+from tests import parity as PR
 
-TOL = 1e-5
+TOL = PR.TOL_STEP
 
 
 def oracle():
@@ -26,7 +28,6 @@ def oracle():
 
 
 def _one_step(pop, q, v, s, **cfg):
-    O = oracle()
     pop32 = pop.as_float32()
     Q, V, Sx = S.state_rows(pop32, q, v, s)
     cs = CP.CpuSim(**cfg)
@@ -35,67 +36,50 @@ def _one_step(pop, q, v, s, **cfg):
     cs.step(1)
     gq, gv, gs, gst = cs.read_state()
     cs.close()
-    keep = {k: val for k, val in cfg.items() if k in ("contact_cap", "box_box", "ground", "actuate",
-                                                       "max_correct_vel", "min_cfm")}
-    prm = O.default_params(**keep)
-    errs = np.zeros((pop.n, 3))
-    margins = np.zeros(pop.n)
-    ost = np.zeros(pop.n, np.uint32)
-    for i in range(pop.n):
-        m = O.model_from_population(pop32, i)
-        nq, nv, ns = O.nq(m), O.nv(m), 2 * (m.nb - 1)
-        s64 = np.zeros(2 * O.MAXB)
-        s64[:ns] = Sx[i, :ns]
-        q64, v64 = Q[i, :nq].astype(np.float64), V[i, :nv].astype(np.float64)
-        oq, ov, os_, st, stats = O.run(m, q64, v64, s64, 1, prm=prm)
-        vfree = O.step_detail(m, q64, v64, s64, prm=prm)["vfree"]
-        margins[i] = stats.margin
-        ost[i] = st
-        sc = (max(np.linalg.norm(oq[:nq]), 1.0), max(np.linalg.norm(ov[:nv]), np.linalg.norm(vfree), 1.0),
-              max(np.linalg.norm(os_[:ns]), 1.0))
-        for j, (a, b) in enumerate(((gq[i, :nq], oq[:nq]), (gv[i, :nv], ov[:nv]), (gs[i, :ns], os_[:ns]))):
-            errs[i, j] = np.linalg.norm(a - b) / sc[j] if len(b) else 0.0
-    near = margins < 1e-5
-    return errs, near, ost, gst
+    prm = PR.oracle_params(**cfg)
+    r = PR.one_step_errors(pop32, Q, V, Sx, gq, gv, gs, prm)
+    y = PR.fp32_yardstick(pop32, Q, V, Sx, prm)
+    return r, y, gst
 
 
-def _check(errs, near, frac_near):
-    bad = (errs.max(axis=1) > TOL) & ~near
-    assert not bad.any(), (errs.max(axis=0), np.nonzero(bad)[0][:10])
-    assert near.mean() <= frac_near
+def _check(name, r, y):
+    fails = PR.parity_failures(r, y)
+    msg = r.summary(name) + " | fp32 " + y.summary("yardstick") + " | " + "; ".join(fails)
+    print(msg)
+    assert not fails, msg
 
 
 def test_one_step_boxes_quadrupeds_grammar():
     pop = P.boxes(48, seed=1)
     q = pop.q0.copy()
     q[:24, 2] = np.random.default_rng(0).uniform(0.03, 0.08, 24)
-    errs, near, ost, gst = _one_step(pop, q, pop.v0, np.zeros((48, 64)))
-    _check(errs, near, 0.1)
-    assert np.array_equal(ost, gst)
+    r, y, gst = _one_step(pop, q, pop.v0, np.zeros((48, 64)))
+    _check("boxes", r, y)
+    assert np.array_equal(r.status_ref, gst)
     pop = P.quadrupeds(48, seed=2)
     q, v, s = P.random_state(pop, seed=5)
     q[:, 2] = np.random.default_rng(1).uniform(0.03, 0.09, pop.n)
-    _check(*_one_step(pop, q, v, s)[:2], 0.1)
+    _check("quadrupeds", *_one_step(pop, q, v, s)[:2])
     pop = P.grammar(96, seed=3)
     q, v, s = P.random_state(pop, seed=7)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(2).uniform(-0.04, 0.0, pop.n)
-    _check(*_one_step(pop, q, v, s)[:2], 0.25)
+    _check("grammar", *_one_step(pop, q, v, s)[:2])
 
 
 def test_one_step_largest_robots_and_the_contact_cap():
     # 26 bodies in random poses: many lattice-aligned bricks sit in exact
-    # separating-axis ties (near-threshold); at least a third are compared
+    # separating-axis ties, compared with the closest valid outcome
     pop = P.grammar(36, seed=51, hinges=(25, 25))
     q, v, s = P.random_state(pop, seed=52)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(53).uniform(-0.03, 0.0, pop.n)
-    _check(*_one_step(pop, q, v, s)[:2], 0.67)
+    _check("grammar-26-bodies", *_one_step(pop, q, v, s)[:2])
     pop = P.grammar(48, seed=61)
     q, v, s = P.random_state(pop, seed=62, angle=0.3)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(63).uniform(-0.045, -0.005, pop.n)
-    errs, near, ost, gst = _one_step(pop, q, v, s, contact_cap=6)
-    _check(errs, near, 0.3)
+    r, y, gst = _one_step(pop, q, v, s, contact_cap=6)
+    _check("cap-6", r, y)
     assert ((gst & S.ST_OVERFLOW) != 0).sum() >= 10
-    assert np.array_equal((gst & S.ST_OVERFLOW) != 0, (ost & S.ST_OVERFLOW) != 0)
+    assert np.array_equal((gst & S.ST_OVERFLOW) != 0, (r.status_ref & S.ST_OVERFLOW) != 0)
 
 
 def test_one_step_settled_grammar_states():
@@ -103,9 +87,7 @@ def test_one_step_settled_grammar_states():
     pop = P.grammar(48, seed=13).as_float32()
     q, v, s, st, _ = O.run_population(pop, pop.q0, pop.v0, P.cpg_initial(pop), 300,
                                       threads=len(os.sched_getaffinity(0)))
-    errs, near, _, _ = _one_step(pop, q, v, s)
-    e = errs.max(axis=1)[~near]
-    assert (e <= 5e-5).all() and (e <= TOL).mean() >= 0.95 and np.median(e) <= 1e-6, errs.max(axis=0)
+    _check("grammar-settled", *_one_step(pop, q, v, s)[:2])
 
 
 def test_contact_free_flight_200_steps():
@@ -219,54 +201,51 @@ def test_one_step_ball_modules_box_and_ball_and_ropes():
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(83).uniform(-0.05, 0.0, pop.n)
     kinds = _sphere_contact_kinds(pop, q)
     assert kinds.min() >= 5, kinds
-    errs, near, ost, gst = _one_step(pop, q, v, s)
-    _check(errs, near, 0.3)
+    _check("ball-modules", *_one_step(pop, q, v, s)[:2])
     pop = P.box_and_ball(48, seed=84)
     q, v, s = P.random_state(pop, seed=85)
     q[:, 2] = np.random.default_rng(86).uniform(0.03, 0.12, pop.n)
-    errs, near, ost, gst = _one_step(pop, q, v, s)
-    _check(errs, near, 0.1)
+    _check("box-and-ball", *_one_step(pop, q, v, s)[:2])
 
 
-def rope_bar(pop, q, errs, near, median_max):
-    """Bar for long chains: M of a 25-link chain has cond(M) ~ 1e5, so FP32's
-    first-order bound on a solve's relative error, cond(M) 2^-24 (~7e-3), is
-    the per-robot limit (measured: at most 0.12 of it) and the median must
-    stay below ``median_max``."""
+def fp32_flight_bar(pop, Q, V, Sx, prm, steps=200):
+    """The contact-free bar of a population lifted into the air: 1e-4 m of
+    core position over ``steps`` steps, or twice the drift of the oracle's own
+    FP32 build from the FP64 oracle where that exceeds 1e-4 m (long chains,
+    cond(M) ~ 1e5, amplify FP32 rounding step after step)."""
+    from oracle import oracle32 as O32
     O = oracle()
-    pop32 = pop.as_float32()
-    e = errs.max(axis=1)
-    for i in np.nonzero(~near)[0]:
-        m = O.model_from_population(pop32, i)
-        cond = np.linalg.cond(O.mass_matrix(m, np.asarray(q[i, :O.nq(m)], np.float64)))
-        assert e[i] <= cond * 2.0 ** -24, (i, e[i], cond)
-    assert np.median(e[~near]) <= median_max, np.median(e[~near])
-    assert near.mean() <= 0.25
+    oq = O.run_population(pop, Q.astype(np.float64), V.astype(np.float64), Sx.astype(np.float64), steps, prm=prm,
+                          threads=PR.ncores())[0]
+    fq = O32.run_population(pop, Q, V, Sx, steps, prm=prm, threads=PR.ncores())[0]
+    drift = np.abs(fq[:, :3] - oq[:, :3]).max()
+    return (1e-4 if drift <= 1e-4 else 2.0 * drift), drift
 
 
-def test_one_step_ropes_against_the_conditioning_bound():
+def test_one_step_ropes_against_the_fp32_yardstick():
     """Ropes of 10 and 25 links (passive), one step from random states
-    pushed into the ground, against the oracle."""
-    for links, med in ((10, 1e-5), (25, 2e-4)):
+    pushed into the ground, against the oracle: cond(M) reaches ~1e5 on 25
+    links, where FP32 arithmetic alone misses 1e-5 on most robots, so the bar
+    is the FP32 yardstick's."""
+    for links in (10, 25):
         pop = P.rope(24, seed=87, links=links)
         q, v, s = P.random_state(pop, seed=88, angle=0.4)
         q[:, 2] = pop.q0[:, 2] + np.random.default_rng(89).uniform(-0.04, 0.0, pop.n)
-        errs, near, ost, gst = _one_step(pop, q, v, s, actuate=0)
-        rope_bar(pop, q, errs, near, med)
+        _check(f"rope-{links}", *_one_step(pop, q, v, s, actuate=0)[:2])
 
 
 def test_ropes_contact_free_and_contact_rich():
-    """Lifted ropes with the servos on, 200 contact-free steps: 10 links keep
-    the contact-free bar (core within 1e-4 m of the oracle); 25 links, whose
-    cond(M) ~ 1e5 amplifies FP32 rounding step after step, drift further and
-    are reported against a sanity bound an order above the measured drift
-    (1.5e-4 m).  Dropped passive 25-link ropes are chaotic and held to the
+    """Lifted ropes with the servos on, 200 contact-free steps: core within
+    1e-4 m of the oracle, or within twice the FP32 yardstick's own drift where
+    that exceeds 1e-4 m (25 links: cond(M) ~ 1e5 amplifies FP32 rounding step
+    after step).  Dropped passive 25-link ropes are chaotic and held to the
     contact-rich bar: population-mean fitness within 2 % after 2000 steps."""
     O = oracle()
     nt = max(1, len(os.sched_getaffinity(0)))
-    for links, bound in ((10, 1e-4), (25, 1e-3)):
+    for links in (10, 25):
         pop = P.lift(P.rope(32, seed=91, links=links), 1.0).as_float32()
         Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
+        bound, drift = fp32_flight_bar(pop, Q, V, Sx, O.default_params(box_box=0))
         cs = CP.CpuSim(box_box=0)
         cs.set_population(pop)
         cs.set_state(Q, V, Sx)
@@ -278,7 +257,8 @@ def test_ropes_contact_free_and_contact_rich():
             oq, ov, os_, _, _ = O.run_population(pop, oq, ov, os_, 50, prm=prm, threads=nt)
             worst = max(worst, np.abs(cs.read_state()[0][:, :3] - oq[:, :3]).max())
         cs.close()
-        assert worst <= bound, (links, worst)
+        print(f"rope-{links} lifted: worst core error {worst:.3g} m, fp32 yardstick drift {drift:.3g} m")
+        assert worst <= bound, (links, worst, drift)
     pop = P.rope(48, seed=92).as_float32()
     Q, V, Sx = S.state_rows(pop, pop.q0, pop.v0, P.cpg_initial(pop))
     cs = CP.CpuSim(actuate=0)
@@ -329,18 +309,17 @@ def test_one_step_single_free_bodies():
     rng = np.random.default_rng(8)
     q = pop.q0.copy()
     q[:, 2] = rng.uniform(0.0, 0.09, pop.n)
-    errs, near, ost, gst = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)))
-    _check(errs, near, 0.1)
-    assert np.array_equal(ost[~near], gst[~near])
-    errs, near, ost, gst = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)), contact_cap=3)
-    _check(errs, near, 0.1)
+    r, y, gst = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)))
+    _check("free-cubes", r, y)
+    assert np.array_equal(r.status_ref, gst)
+    r, y, gst = _one_step(pop, q, pop.v0, np.zeros((pop.n, 64)), contact_cap=3)
+    _check("free-cubes-cap3", r, y)
     assert ((gst & 2) != 0).sum() >= 5
     balls = P.boxes(32, seed=9, vel_sigma=2.0)
     balls.geom[:, 0] = P.GEOM_SPHERE
     qb = balls.q0.copy()
     qb[:, 2] = rng.uniform(0.03, 0.06, balls.n)
-    errs, near, ost, gst = _one_step(balls, qb, balls.v0, np.zeros((balls.n, 64)))
-    _check(errs, near, 0.1)
+    _check("free-balls", *_one_step(balls, qb, balls.v0, np.zeros((balls.n, 64)))[:2])
 
 
 def test_free_body_closed_form_matches_the_general_step():

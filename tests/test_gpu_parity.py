@@ -1,47 +1,32 @@
 """CUDA path vs the FP64 oracle, through the C ABI.
 
-Tolerances:
-  * one step from identical FP32-rounded states: per variant
-    |dx| / scale(x) <= 1e-5 for each of q, v and the CPG state, with
-    scale = max(|x_ref|, 1) for q and the CPG state and
-    scale = max(|v_ref|, |v_free_ref|, 1) for v: a step's velocity is the
-    unconstrained velocity v_free plus a contact correction of the same
-    size (a brick pressed into the ground by its servo: ~6 rad/s each, nearly
-    cancelling), and FP32 resolves the result only relative to those terms
-    (about cond(L) * 2^-24 * |v_free - v+|);
-  * contact-free robots (lifted 1 m, 200 steps): core position error
-    <= 1e-4 m;
-  * contact-rich runs (chaotic): population-mean fitness within 2 %.
-Variants whose step contains a discrete decision (contact activation, SAT
-axis, clipping side, overflow cut) within 1e-5 of its threshold in the oracle
-are near-threshold: FP32 and FP64 may legitimately take different branches
-there.  They are counted and reported, and must stay a small minority.
+One step from identical FP32-rounded states (tests/parity.py): per robot the
+error against the closest valid outcome of the oracle's step (decisions within
+1e-5 of their thresholds taken either way), as |dx| / max(|x_ref|, 1) for each
+of q, v and the CPG state (the stated 1e-5 bar) and as the worst single entry;
+every robot is compared.  Where FP32 arithmetic itself meets 1e-5 on every
+robot of the states (the oracle's FP32 build on the same states), the GPU must
+too; on ill-conditioned states (settled, servo-loaded robots) the GPU's error
+distribution may be no worse than that FP32 yardstick's.  Contact-free robots
+(lifted 1 m): core position within 1e-4 m over 200 steps.  Contact-rich runs
+(chaotic): population-mean fitness within 2 %.
 """
-import os
-
 import numpy as np
 import pytest
 
 from paper_2502_11129_b300 import population as P
 from paper_2502_11129_b300 import sim as S
+from tests import parity as PR
 
 pytestmark = pytest.mark.gpu
 
-TOL_STEP = 1e-5
-MARGIN = 1e-5
-# settled, servo-loaded robots: cond(M) ~ 2e4, so an FP32 solve carries up to
-# cond * 2^-24 ~ 1e-3 relative error; the bar is median <= 1e-6, >= 95 % of
-# the robots within TOL_STEP and none above this
-TOL_SETTLED_MAX = 5e-5
+MARGIN = PR.BAND
+ncores = PR.ncores
 
 
 def oracle():
     from oracle import oracle as O
     return O
-
-
-def ncores():
-    return max(1, len(os.sched_getaffinity(0)))
 
 
 def _gpu_sim(pop, **cfg):
@@ -50,104 +35,80 @@ def _gpu_sim(pop, **cfg):
     return sm
 
 
-def _oracle_params(O, **cfg):
-    keep = {k: v for k, v in cfg.items() if k in ("dt", "gravity", "pgs_iters", "mu", "contact_cap",
-                                                 "ground", "box_box", "actuate", "armature",
-                                                 "max_correct_vel", "min_cfm")}
-    return O.default_params(**keep)
-
-
 def _one_step(pop, q, v, s, **cfg):
-    """Returns per-variant relative errors of q, v, s and oracle margins."""
-    O = oracle()
+    """One GPU step from the FP32-rounded states; returns (errors against the
+    oracle's closest valid outcome, FP32 yardstick errors, GPU status bits,
+    the simulator)."""
     pop32 = pop.as_float32()
     Q, V, Sx = S.state_rows(pop32, q, v, s)
     sm = _gpu_sim(pop32, **cfg)
     sm.set_state(Q, V, Sx)
     sm.step(1)
     gq, gv, gs, gst = sm.read_state()
-    prm = _oracle_params(O, **cfg)
-    errs = np.zeros((pop.n, 3))
-    margins = np.zeros(pop.n)
-    ost = np.zeros(pop.n, np.uint32)
-    for i in range(pop.n):
-        m = O.model_from_population(pop32, i)
-        nq, nv, ns = O.nq(m), O.nv(m), 2 * (m.nb - 1)
-        s64 = np.zeros(2 * O.MAXB)
-        s64[:ns] = Sx[i, :ns]
-        q64, v64 = Q[i, :nq].astype(np.float64), V[i, :nv].astype(np.float64)
-        oq, ov, os_, st, stats = O.run(m, q64, v64, s64, 1, prm=prm)
-        vfree = O.step_detail(m, q64, v64, s64, prm=prm)["vfree"]
-        margins[i] = stats.margin
-        ost[i] = st
-        scales = (max(np.linalg.norm(oq[:nq]), 1.0),
-                  max(np.linalg.norm(ov[:nv]), np.linalg.norm(vfree), 1.0),
-                  max(np.linalg.norm(os_[:ns]), 1.0))
-        for j, (a, b) in enumerate(((gq[i, :nq], oq[:nq]), (gv[i, :nv], ov[:nv]), (gs[i, :ns], os_[:ns]))):
-            errs[i, j] = np.linalg.norm(a - b) / scales[j] if len(b) else 0.0
-    return errs, margins, ost, gst, sm
+    prm = PR.oracle_params(**cfg)
+    r = PR.one_step_errors(pop32, Q, V, Sx, gq, gv, gs, prm)
+    y = PR.fp32_yardstick(pop32, Q, V, Sx, prm)
+    return r, y, gst, sm
 
 
-def _report(name, errs, margins):
-    near = margins < MARGIN
-    bad = (errs.max(axis=1) > TOL_STEP) & ~near
-    msg = (f"{name}: n={len(errs)} near-threshold={near.sum()} worst(q,v,s)={errs.max(axis=0)} "
-           f"worst-away-from-threshold={errs[~near].max(axis=0) if (~near).any() else None} "
-           f"failing={np.nonzero(bad)[0][:10]}")
+def _check(name, r, y):
+    fails = PR.parity_failures(r, y)
+    msg = r.summary(name) + " | fp32 " + y.summary("yardstick") + " | " + "; ".join(fails)
     print(msg)
-    return near, bad, msg
+    assert not fails, msg
 
 
 def test_one_step_free_boxes():
     pop = P.boxes(64, seed=1)
     q = pop.q0.copy()
     q[:32, 2] = np.random.default_rng(0).uniform(0.03, 0.08, 32)  # half of them in contact
-    errs, margins, ost, gst, _ = _one_step(pop, q, pop.v0, np.zeros((64, 64)))
-    near, bad, msg = _report("boxes", errs, margins)
-    assert not bad.any(), msg
-    assert near.mean() < 0.1, msg
-    assert np.array_equal(ost[~near], gst[~near])
+    r, y, gst, _ = _one_step(pop, q, pop.v0, np.zeros((64, 64)))
+    _check("boxes", r, y)
+    assert np.array_equal(r.status_ref, gst)
 
 
 def test_one_step_quadrupeds_random_states():
     pop = P.quadrupeds(128, seed=2)
     q, v, s = P.random_state(pop, seed=5)
     q[:, 2] = np.random.default_rng(1).uniform(0.03, 0.09, pop.n)
-    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
-    near, bad, msg = _report("quadrupeds", errs, margins)
-    assert not bad.any(), msg
-    assert near.mean() < 0.1, msg
+    r, y, gst, _ = _one_step(pop, q, v, s)
+    _check("quadrupeds", r, y)
 
 
 def test_one_step_grammar_random_states():
     pop = P.grammar(256, seed=3)
     q, v, s = P.random_state(pop, seed=7)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(2).uniform(-0.04, 0.0, pop.n)
-    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
-    near, bad, msg = _report("grammar", errs, margins)
-    assert not bad.any(), msg
-    # random hinge angles put many lattice-aligned bricks in exact SAT ties
-    assert near.mean() < 0.25, msg
+    r, y, gst, _ = _one_step(pop, q, v, s)
+    _check("grammar", r, y)
 
 
 def test_one_step_grammar_zero_pose_settled_by_oracle():
-    """States taken from an oracle run (realistic contact sets) at step 300."""
+    """States taken from an oracle run (realistic contact sets) at step 300:
+    resting, servo-loaded robots whose mass matrices reach cond ~ 2e4, where
+    FP32 arithmetic alone does not hold 1e-5 on every robot."""
     O = oracle()
     pop = P.grammar(96, seed=13).as_float32()
     q, v, s, st, _ = O.run_population(pop, pop.q0, pop.v0, P.cpg_initial(pop), 300, threads=ncores())
-    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
-    near, bad, msg = _report("grammar-settled", errs, margins)
-    # resting, servo-loaded robots: cond(M) ~ 2e4, so FP32's worst-case bound
-    # cond * 2^-24 is ~1e-3; the measured errors sit two orders below it.
-    # Bar: median <= 1e-6, >= 95 % of the robots within 1e-5, none above 2e-5.
-    e = errs.max(axis=1)[~near]
-    assert (e <= TOL_SETTLED_MAX).all(), msg
-    assert (e <= TOL_STEP).mean() >= 0.95, msg
-    assert np.median(e) <= 1e-6, msg
+    r, y, gst, _ = _one_step(pop, q, v, s)
+    _check("grammar-settled", r, y)
+
+
+def contact_list_matches(g, outs, origin):
+    """The GPU's contact list equals one of the valid oracle lists: counts,
+    bodies and order exactly, depths and points to 1e-5, normals to 1e-4."""
+    for c in outs:
+        if (g["n"] == len(c["a"]) and np.array_equal(g["a"], c["a"]) and np.array_equal(g["b"], c["b"])
+                and np.allclose(g["depth"], c["depth"], atol=1e-5) and np.allclose(g["nrm"], c["n"], atol=1e-4)
+                and np.allclose(g["p"], c["p"] - origin, atol=1e-5)):
+            return True
+    return False
 
 
 def test_contact_lists_match_oracle():
-    """Contact generation (counts, bodies, order bit-exact; geometry to 1e-5)."""
+    """Contact generation, every robot: counts, bodies and order exact,
+    geometry to 1e-5, against the oracle's list or, where a decision lies
+    within 1e-5 of its threshold, one of its valid lists."""
     O = oracle()
     pop = P.grammar(64, seed=31).as_float32()
     q, v, s = P.random_state(pop, seed=9, angle=1.0)
@@ -157,20 +118,14 @@ def test_contact_lists_match_oracle():
     sm.set_state(Q, V, Sx)
     sm.step(1)
     prm = O.default_params()
-    checked = 0
+    near = 0
     for i in range(pop.n):
         m = O.model_from_population(pop, i)
-        c = O.contacts(m, Q[i, :O.nq(m)].astype(np.float64), prm)
-        if c["margin"] < MARGIN:
-            continue
+        outs, k, complete = O.contact_outcomes(m, Q[i, :O.nq(m)].astype(np.float64), MARGIN, prm)
+        near += k > 0
         g = sm.debug_contacts(i)
-        assert g["n"] == len(c["a"]), (i, g["n"], len(c["a"]))
-        assert np.array_equal(g["a"], c["a"]) and np.array_equal(g["b"], c["b"]), i
-        assert np.allclose(g["depth"], c["depth"], atol=1e-5), i
-        assert np.allclose(g["nrm"], c["n"], atol=1e-4), i
-        assert np.allclose(g["p"], c["p"] - Q[i, :3], atol=1e-5), i
-        checked += 1
-    assert checked > pop.n // 2
+        assert contact_list_matches(g, outs, Q[i, :3]), (i, g["n"], [len(c["a"]) for c in outs[:8]], complete)
+    print("contact lists: robots with near-threshold decisions", near, "of", pop.n)
 
 
 def test_contact_free_trajectories_200_steps():
@@ -326,12 +281,10 @@ def test_one_step_largest_robots_26_bodies():
     assert (pop.nb == S.SIM_MAX_BODIES).all()
     q, v, s = P.random_state(pop, seed=52)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(53).uniform(-0.03, 0.0, pop.n)
-    errs, margins, ost, gst, _ = _one_step(pop, q, v, s)
-    near, bad, msg = _report("grammar-26-bodies", errs, margins)
-    assert not bad.any(), msg
+    r, y, gst, _ = _one_step(pop, q, v, s)
     # lattice-aligned bricks in random poses sit in exact separating-axis
-    # ties (near-threshold); at least a third of the robots are compared
-    assert near.mean() <= 0.67, msg
+    # ties: those robots are compared with the closest valid outcome
+    _check("grammar-26-bodies", r, y)
 
 
 def _contact_counts(sm, n):
@@ -346,19 +299,17 @@ def test_one_step_both_sweep_paths_and_the_contact_cap():
     pop = P.grammar(128, seed=61)
     q, v, s = P.random_state(pop, seed=62, angle=0.3)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(63).uniform(-0.06, -0.005, pop.n)
-    errs, margins, ost, gst, sm = _one_step(pop, q, v, s)
+    r, y, gst, sm = _one_step(pop, q, v, s)
     nc = _contact_counts(sm, pop.n)
     print("contact counts", np.bincount(nc))
     assert (nc <= 10).sum() >= 10 and (nc > 10).sum() >= 10, np.bincount(nc)
-    near, bad, msg = _report("both-sweeps", errs, margins)
-    assert not bad.any(), msg
-    errs, margins, ost, gst, sm = _one_step(pop, q, v, s, contact_cap=6)
+    _check("both-sweeps", r, y)
+    r, y, gst, sm = _one_step(pop, q, v, s, contact_cap=6)
     nc = _contact_counts(sm, pop.n)
     over = (gst & S.ST_OVERFLOW) != 0
     assert over.sum() >= 20 and (nc <= 6).all()
-    assert np.array_equal(over, (ost & S.ST_OVERFLOW) != 0)
-    near, bad, msg = _report("cap-6", errs, margins)
-    assert not bad.any(), msg
+    assert np.array_equal(over, (r.status_ref & S.ST_OVERFLOW) != 0)
+    _check("cap-6", r, y)
 
 
 def test_empty_and_ragged_inputs():
@@ -391,7 +342,8 @@ def test_bench_workload_full_size_sampled_one_step():
     bench's launch configuration (autotuned shape, 500-step launches, CUDA
     graph, slowest-first order): after 1000 steps, one more step of every
     16th robot from the GPU's FP32 state against the oracle from the same
-    state (the settled-robot bar)."""
+    state (the bars of tests/parity.py: settled robots, the FP32
+    yardstick)."""
     O = oracle()
     pop = P.grammar(4096, seed=3).as_float32()
     s0 = P.cpg_initial(pop)
@@ -406,13 +358,9 @@ def test_bench_workload_full_size_sampled_one_step():
     idx = np.arange(0, 4096, 16)
     idx = idx[(st1[idx] & 5) == 0]
     sub = pop.subset(idx)
-    errs, margins, ost, gst, _ = _one_step(sub, Q1[idx].astype(np.float64), V1[idx].astype(np.float64),
-                                           S1[idx].astype(np.float64))
-    near, bad, msg = _report("bench-4096-sampled", errs, margins)
-    e = errs.max(axis=1)[~near]
-    assert (e <= TOL_SETTLED_MAX).all(), msg
-    assert (e <= TOL_STEP).mean() >= 0.95, msg
-    assert np.median(e) <= 1e-6, msg
+    r, y, gst, _ = _one_step(sub, Q1[idx].astype(np.float64), V1[idx].astype(np.float64),
+                             S1[idx].astype(np.float64))
+    _check("bench-4096-sampled", r, y)
 
 
 @pytest.mark.parametrize("alpha_deg,slides", [(20.0, False), (35.0, True)])
