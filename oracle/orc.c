@@ -861,6 +861,27 @@ static void tangent_basis(work* w, const real* n, real* t1, real* t2) {
     FL(w, 2 + 2 + 4 + 2 + 1 + 3 + 1);
 }
 
+/* Tangents of a body-pair contact: Duff's basis built in the fixed frame G
+ * whose rows are g1 = (-sqrt(2/3), sqrt(1/3), 0), g2 = (-1/sqrt6, -1/sqrt3,
+ * 1/sqrt2), g3 = (1, sqrt2, sqrt3)/sqrt6, then turned back (reading: the
+ * basis jumps where (G n)_z changes sign, on normals orthogonal to g3, instead
+ * of on the horizontal normals lattice-built bricks side by side produce;
+ * the Gauss-Seidel result depends on the basis).  Ground contacts keep
+ * tangent_basis: x and y. */
+static void pair_tangent_basis(work* w, const real* n, real* t1, real* t2) {
+    const real r2 = sqrt(2.0), r3 = sqrt(3.0), r6 = sqrt(6.0);
+    const real G[3][3] = {{-r2 / r3, 1.0 / r3, 0.0}, {-1.0 / r6, -1.0 / r3, 1.0 / r2}, {1.0 / r6, r2 / r6, r3 / r6}};
+    real m[3], u1[3], u2[3];
+    for (int i = 0; i < 3; ++i) m[i] = G[i][0] * n[0] + G[i][1] * n[1] + G[i][2] * n[2];
+    FL(w, 15);
+    tangent_basis(w, m, u1, u2);
+    for (int k = 0; k < 3; ++k) {
+        t1[k] = G[0][k] * u1[0] + G[1][k] * u1[1] + G[2][k] * u1[2];
+        t2[k] = G[0][k] * u2[0] + G[1][k] * u2[1] + G[2][k] * u2[2];
+    }
+    FL(w, 30);
+}
+
 /* is body k (>= 1) the body x or one of its ancestors? */
 static int on_path(const orc_model* m, int x, int k) {
     for (int y = x; y > 0; y = m->parent[y]) if (y == k) return 1;
@@ -987,7 +1008,8 @@ static int step(work* w, const orc_model* m, const orc_params* prm, real* q, rea
     for (int k = 0; k < nc; ++k) {
         real t1[3], t2[3];
         const real* n = w->con.nrm[k];
-        tangent_basis(w, n, t1, t2);
+        if (w->con.b[k] < 0) tangent_basis(w, n, t1, t2);
+        else pair_tangent_basis(w, n, t1, t2);
         const real* dirs[3] = {n, t1, t2};
         for (int d = 0; d < 3; ++d) {
             int r = 3 * k + d;

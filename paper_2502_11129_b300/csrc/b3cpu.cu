@@ -359,7 +359,8 @@ bool step_robot(const Robot& m, const uint16_t* pairs, const StepParams& P, floa
     const unsigned pa = path[a], pb = b == 255 ? 0u : path[b];
     const float sroot = (b == 255) ? 1.f : 0.f;
     float t1[3], t2[3], d[3];
-    tangent_basis(nrm, t1, t2);
+    if (b == 255) tangent_basis(nrm, t1, t2);
+    else pair_tangent_basis(nrm, t1, t2);
     for (int t = 0; t < 3; ++t) d[t] = dir == 0 ? nrm[t] : (dir == 1 ? t1[t] : t2[t]);
     float wa[3];
     cross3(pr, d, wa);

@@ -438,13 +438,35 @@ __host__ __device__ __forceinline__ void sincos_f64(double x, double* s_out, dou
   *c_out = ((q + 1) & 2) ? -ca : ca;
 }
 
-// Duff et al. 2017 ("Building an Orthonormal Basis, Revisited"), JCGT 6(1)
+// Duff et al. 2017 ("Building an Orthonormal Basis, Revisited"), JCGT 6(1);
+// ground contacts (n = +z) get x and y from it
 __host__ __device__ __forceinline__ void tangent_basis(const float* n, float* t1, float* t2) {
   float s = n[2] >= 0.f ? 1.f : -1.f;
   float a = -1.f / (s + n[2]);
   float b = n[0] * n[1] * a;
   t1[0] = 1.f + s * n[0] * n[0] * a; t1[1] = s * b; t1[2] = -s * n[0];
   t2[0] = b; t2[1] = s + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+// Tangent directions of a body-pair contact: the same basis built in a fixed
+// frame G (rows g1, g2, g3, g3 = (1, sqrt 2, sqrt 3) / sqrt 6) and turned back.
+// No basis field on the sphere of normals is continuous everywhere; Duff's
+// jumps where n_z changes sign, i.e. on horizontal normals, which bricks
+// built on a lattice and lying side by side produce exactly, and the
+// Gauss-Seidel result depends on the basis (each tangent row has its own
+// step).  In G the jump lies on the normals orthogonal to g3, which no
+// lattice direction is.
+__host__ __device__ __forceinline__ void pair_tangent_basis(const float* n, float* t1, float* t2) {
+  constexpr float kG[3][3] = {{-0.816496580927726f, 0.577350269189626f, 0.f},
+                              {-0.408248290463863f, -0.577350269189626f, 0.707106781186548f},
+                              {0.408248290463863f, 0.577350269189626f, 0.707106781186548f}};
+  float m[3], u1[3], u2[3];
+  for (int i = 0; i < 3; ++i) m[i] = kG[i][0] * n[0] + kG[i][1] * n[1] + kG[i][2] * n[2];
+  tangent_basis(m, u1, u2);
+  for (int k = 0; k < 3; ++k) {
+    t1[k] = kG[0][k] * u1[0] + kG[1][k] * u1[1] + kG[2][k] * u1[2];
+    t2[k] = kG[0][k] * u2[0] + kG[1][k] * u2[1] + kG[2][k] * u2[2];
+  }
 }
 
 }  // namespace b3

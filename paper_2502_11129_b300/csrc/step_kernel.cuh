@@ -683,7 +683,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         pb = b == 255 ? 0u : sm.path[b];
         sroot = (b == 255) ? 1.f : 0.f;
         float t1[3], t2[3];
-        tangent_basis(nrm, t1, t2);
+        if (b == 255) tangent_basis(nrm, t1, t2);
+        else pair_tangent_basis(nrm, t1, t2);
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = dir == 0 ? nrm[q] : (dir == 1 ? t1[q] : t2[q]);
       }
