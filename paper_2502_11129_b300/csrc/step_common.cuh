@@ -185,6 +185,9 @@ __host__ __device__ __noinline__ int box_box_lane(const float (*RR)[32], const f
         rB += hB[k] * fabsf(dot3(Bx[k], L));
       }
       const float ov = rA + rB - fabsf(dot3(D, L));
+      // a separating axis ends the test: the pair has no contact (the same
+      // verdict as the minimum over all 15 axes being <= 0)
+      if (!(ov > 0.f)) return 0;
       if (e == 0 || ov < min_ov) min_ov = ov;
       if (e < 6) {
         if (fi < 0 || ov < fbest) { fbest = ov; fi = e; }

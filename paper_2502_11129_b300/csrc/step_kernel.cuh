@@ -846,18 +846,17 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       __syncwarp();
       float w = w_row;
-      float4 ca = cS[0], cb4 = cS[1], cc4 = cS[2];
-      float an = sm.Yt[0][lane], a1 = sm.Yt[1][lane], a2 = sm.Yt[2][lane];
       float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of the contact being updated
       const int nupd = P.iters * nc;
       int k = 0;
-#pragma unroll 2
       for (int upd = 0; upd < nupd; ++upd) {
         const int kn = (k + 1 < nc) ? k + 1 : 0;
-        const float nan0 = sm.Yt[3 * kn][lane], na1 = sm.Yt[3 * kn + 1][lane], na2 = sm.Yt[3 * kn + 2][lane];
-        const float4 na = cS[3 * kn], nb4 = cS[3 * kn + 1], nc4 = cS[3 * kn + 2];
-        const float4 nl = lamS[kn];  // the next contact's impulses (stale only when kn == k)
         const int r = 3 * k;
+        // this contact's constants and this lane's row of A in its columns
+        // (loaded first, used after the shuffles), the next one's impulses
+        const float4 ca = cS[r], cb4 = cS[r + 1], cc4 = cS[r + 2];
+        const float an = sm.Yt[r][lane], a1 = sm.Yt[r + 1][lane], a2 = sm.Yt[r + 2][lane];
+        const float4 nl = lamS[kn];  // stale only when kn == k
         const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
         const float gn = wn + ca.z * ln;
         const float lnn = fmaxf(0.f, ln - gn * ca.y);
@@ -877,8 +876,6 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         ln = same ? lnn : nl.x;
         l1 = same ? l1t : nl.y;
         l2 = same ? l2t : nl.z;
-        an = nan0; a1 = na1; a2 = na2;
-        ca = na; cb4 = nb4; cc4 = nc4;
         k = kn;
       }
       __syncwarp();
@@ -904,21 +901,24 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int k0 = lane; k0 < nc; k0 += 32) lamS[k0] = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncwarp();
       const float4* c4 = reinterpret_cast<const float4*>(cstg);
-      int k = 0, kn = nc > 1 ? 1 : 0;
+      // more than 10 contacts here: the next contact is never the current one
+      int k = 0, kn = 1;
       float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
       const float* Zn = Yg + (size_t)(3 * kn) * 32;
       float z0 = Zn[lane], z1 = Zn[32 + lane], z2 = Zn[64 + lane];
-      float4 ca = c4[0], cb4 = c4[1], cc4 = c4[2];
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // Y_k . u before update k (u = 0 at the start)
       float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of contact k
       const int nupd = P.iters * nc;
       for (int upd = 0; upd < nupd; ++upd) {
         const int knn = (kn + 1 < nc) ? kn + 1 : 0;
+        // this contact's constants and coupling block B_k (loaded first, used
+        // after the reduction's shuffles); the next one's impulses and the
+        // rows after it
+        const float4 ca = c4[6 * k], cb4 = c4[6 * k + 1], cc4 = c4[6 * k + 2];
+        const float4 bq0 = c4[6 * k + 3], bq1 = c4[6 * k + 4], bq2 = c4[6 * k + 5];
+        const float4 nl = lamS[kn];
         const float* Zz = Yg + (size_t)(3 * knn) * 32;
         const float zz0 = Zz[lane], zz1 = Zz[32 + lane], zz2 = Zz[64 + lane];
-        const float4 na = c4[6 * kn], nb4 = c4[6 * kn + 1], nc4 = c4[6 * kn + 2];
-        const float4 bq0 = c4[6 * k + 3], bq1 = c4[6 * k + 4], bq2 = c4[6 * k + 5];
-        const float4 nl = lamS[kn];  // stale only when kn == k
         // the next contact's row products against u before this update
         float p0 = z0 * u, p1 = z1 * u, p2 = z2 * u;
         warp_sum3(p0, p1, p2, lane);
@@ -942,13 +942,11 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         s0 = p0 + bq0.x * dn + bq0.y * d1 + bq0.z * d2;
         s1 = p1 + bq0.w * dn + bq1.x * d1 + bq1.y * d2;
         s2 = p2 + bq1.z * dn + bq1.w * d1 + bq2.x * d2;
-        const bool same = kn == k;
-        ln = same ? lnn : nl.x;
-        l1 = same ? l1t : nl.y;
-        l2 = same ? l2t : nl.z;
+        ln = nl.x;
+        l1 = nl.y;
+        l2 = nl.z;
         y0 = z0; y1 = z1; y2 = z2;
         z0 = zz0; z1 = zz1; z2 = zz2;
-        ca = na; cb4 = nb4; cc4 = nc4;
         k = kn;
         kn = knn;
       }
