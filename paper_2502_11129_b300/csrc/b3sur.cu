@@ -67,6 +67,9 @@ enum Epi { EPI_F32 = 0, EPI_BIAS_RELU_BF16 = 1 };
 // give-up sets a device flag that the host checks after its next
 // synchronisation.
 constexpr int UM_M = 128, UM_KC = 64, UM_STAGES = 2, UM_MAXPARTS = 3;
+// the weight gradients reduce over the batch (K up to the batch size): their
+// K is split over up to this many CTAs per 128-row tile
+constexpr int UM_MAXSPLIT = 16;
 constexpr int UM_A_SLICE = UM_M * 16;  // bytes per 8-wide K slice of A
 // requested dynamic shared memory: at most two CTAs per SM, so their tensor-
 // memory columns (at most 2 x 256) always fit the SM's 512 and an
@@ -87,6 +90,8 @@ struct UmmaShape {
 
 struct UmmaArgs {
   int M, K, parts;   // K a multiple of UM_KC; parts 1..UM_MAXPARTS operand pairs
+  int kslice;        // K chunks per CTA along gridDim.y (split K); every CTA has at least one
+  long part_stride;  // split K: CTA y writes its FP32 partial to Cf + y * part_stride
   const float* bias; // EPI_BIAS_RELU_BF16
   float* Cf;         // EPI_F32 output, row stride BN
   bf16* Cb;          // EPI_BIAS_RELU_BF16 outputs (hi, lo), row stride BN
@@ -158,11 +163,13 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ UmmaMap
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const int nk = g.K / UM_KC, nchunks = g.parts * nk;
+  // this CTA's K chunks: kc0 .. kc0 + nk - 1 of every operand pair
+  const int nk_all = g.K / UM_KC, kc0 = blockIdx.y * g.kslice;
+  const int nk = min(g.kslice, nk_all - kc0), nchunks = g.parts * nk;
   if (tid == 0) {
     const uint32_t ring = smem_u32(um_smem);
     auto load = [&](int c) {
-      const int s = c % UM_STAGES, part = c / nk, k0 = (c % nk) * UM_KC;
+      const int s = c % UM_STAGES, part = c / nk, k0 = (kc0 + c % nk) * UM_KC;
       const uint32_t a = ring + s * Sh::STAGE, b = a + Sh::A_STAGE, bar = smem_u32(&full_bar[s]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(Sh::STAGE) : "memory");
       for (int j = 0; j < UM_KC / 8; ++j) {
@@ -226,7 +233,7 @@ __global__ void __launch_bounds__(128) gemm_umma(const __grid_constant__ UmmaMap
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row >= g.M) continue;
       if (g.epi == EPI_F32) {
-        float4* o = reinterpret_cast<float4*>(g.Cf + (size_t)row * BN + c0);
+        float4* o = reinterpret_cast<float4*>(g.Cf + blockIdx.y * g.part_stride + (size_t)row * BN + c0);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
@@ -271,6 +278,18 @@ __global__ void transpose_pad(const bf16* __restrict__ src, int rows, int cols, 
   }
 }
 
+// split-K: out[i] = sum over the S partials, in partial order (deterministic)
+__global__ void splitk_sum(const float4* __restrict__ part, int S, long n4, float4* __restrict__ out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  float4 a = part[i];
+  for (int y = 1; y < S; ++y) {
+    const float4 b = part[(long)y * n4 + i];
+    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+  }
+  out[i] = a;
+}
+
 // h = relu(z + b) as FP32 and as a BF16 pair (hi, lo)
 __global__ void bias_relu_split(const float* __restrict__ z, const float* __restrict__ b, int n, float* hf, bf16* hi_out,
                                 bf16* lo_out) {
@@ -313,6 +332,13 @@ __global__ void loss_grad(const float* __restrict__ y, const float* __restrict__
     __syncthreads();
   }
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// acc += the batch's squared-error partials (one thread, fixed order)
+__global__ void loss_accumulate(const float* __restrict__ part, int nblk, double* acc) {
+  double s = *acc;
+  for (int q = 0; q < nblk; ++q) s += part[q];
+  *acc = s;
 }
 
 // dZ2 = dy * W3 * (H2 > 0) as a BF16 pair (hi, lo = remainder) for the next GEMMs
@@ -385,11 +411,22 @@ __global__ void col_sums(const float* __restrict__ dy, const bf16* __restrict__ 
   }
 }
 
+// Adam's step count lives on the device (so that a captured training epoch
+// replays with the right bias corrections): advance it and compute
+// 1 - b1^t, 1 - b2^t in FP64, rounded to FP32
+__global__ void adam_prep(long long* step, double b1, double b2, float* bc) {
+  const long long t = *step + 1;
+  *step = t;
+  bc[0] = (float)(1.0 - pow(b1, (double)t));
+  bc[1] = (float)(1.0 - pow(b2, (double)t));
+}
+
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float bc1,
-                            float bc2) {
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
+                            const float* __restrict__ bc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const float bc1 = bc[0], bc2 = bc[1];
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -597,6 +634,13 @@ struct sur_ctx {
   int* idx = nullptr;
   size_t cap_scores = 0;
   int* uerr = nullptr;     // set by gemm_umma when a tensor-core wait gives up
+  float* kpart = nullptr;  // split-K partials of the weight gradients (UM_MAXSPLIT x HID x HID)
+  long long* dstep = nullptr;  // Adam's step count (device)
+  float* bc = nullptr;         // its bias corrections 1 - b1^t, 1 - b2^t
+  double* loss_acc = nullptr;  // sum of squared errors of an epoch (device)
+  // one captured training epoch (batches of the permuted set), keyed by (n, batch)
+  cudaGraphExec_t epoch_graph = nullptr;
+  int graph_n = 0, graph_batch = 0;
   // K-major (transposed) copies of the backward operands: [column][batch row],
   // row stride SUR_MAX_BATCH, batch rows padded with zeros to a multiple of 64
   bf16* dz2T = nullptr;
@@ -649,7 +693,7 @@ cudaError_t refresh_bf16(sur_ctx* c) {
 
 template <int BN>
 cudaError_t launch_umma(sur_ctx* c, int M, int K, std::initializer_list<const CUtensorMap*> a,
-                        std::initializer_list<const CUtensorMap*> b, UmmaArgs g) {
+                        std::initializer_list<const CUtensorMap*> b, UmmaArgs g, int splits = 1) {
   UmmaMaps maps{};
   int p = 0;
   for (const CUtensorMap* m : a) maps.a[p++] = *m;
@@ -659,7 +703,23 @@ cudaError_t launch_umma(sur_ctx* c, int M, int K, std::initializer_list<const CU
   g.K = K;
   g.parts = p;
   g.err = c->uerr;
-  gemm_umma<BN><<<(M + UM_M - 1) / UM_M, 128, UM_SMEM, c->stream>>>(maps, g);
+  const int nk = K / UM_KC;
+  g.kslice = (nk + splits - 1) / splits;
+  const int sy = (nk + g.kslice - 1) / g.kslice;  // every CTA row gets at least one chunk
+  g.part_stride = 0;
+  float* dst = g.Cf;
+  if (sy > 1) {
+    // the CTAs of one 128-row tile split K; each writes an FP32 partial,
+    // then one pass sums them in a fixed order
+    g.Cf = c->kpart;
+    g.part_stride = (long)M * BN;
+  }
+  gemm_umma<BN><<<dim3((M + UM_M - 1) / UM_M, sy), 128, UM_SMEM, c->stream>>>(maps, g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sy == 1) return e;
+  const long n4 = (long)M * BN / 4;
+  splitk_sum<<<(int)((n4 + 255) / 256), 256, 0, c->stream>>>(reinterpret_cast<const float4*>(c->kpart), sy, n4,
+                                                            reinterpret_cast<float4*>(dst));
   return cudaGetLastError();
 }
 
@@ -705,7 +765,7 @@ cudaError_t backward_batch(sur_ctx* c, int n) {
   UmmaArgs g{};
   g.Cf = c->g + OW2; g.epi = EPI_F32;
   e = launch_umma<HID>(c, HID, kp, {&c->tm_dz2T, &c->tm_dz2loT, &c->tm_dz2T}, {&c->tm_h1T, &c->tm_h1T, &c->tm_h1loT},
-                       g);
+                       g, UM_MAXSPLIT);
   if (e != cudaSuccess) return e;
   // dH1(m, j) = sum_i dZ2(m, i) W2(i, j): both parts of dZ2 against W2 transposed
   UmmaArgs h{};
@@ -721,18 +781,17 @@ cudaError_t backward_batch(sur_ctx* c, int n) {
   // dW1(i, j) = sum_m dZ1(m, i) X(m, j): both parts of dZ1
   UmmaArgs w{};
   w.Cf = c->g + OW1; w.epi = EPI_F32;
-  e = launch_umma<IN>(c, HID, kp, {&c->tm_dz1T, &c->tm_dz1loT}, {&c->tm_xT, &c->tm_xT}, w);
+  e = launch_umma<IN>(c, HID, kp, {&c->tm_dz1T, &c->tm_dz1loT}, {&c->tm_xT, &c->tm_xT}, w, UM_MAXSPLIT);
   if (e != cudaSuccess) return e;
   col_sums<<<HID / 32 + 1, dim3(32, 8), 0, c->stream>>>(c->dy, c->w3b, c->h2f, c->dz1f, n, c->g);
   return cudaGetLastError();
 }
 
 cudaError_t adam_update(sur_ctx* c) {
-  c->step += 1;
-  const double bc1 = 1.0 - std::pow((double)c->cfg.beta1, (double)c->step);
-  const double bc2 = 1.0 - std::pow((double)c->cfg.beta2, (double)c->step);
+  c->step += 1;  // host mirror of the device count
+  adam_prep<<<1, 1, 0, c->stream>>>(c->dstep, (double)c->cfg.beta1, (double)c->cfg.beta2, c->bc);
   adam_kernel<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->p, c->g, c->m, c->v, NP, c->cfg.lr, c->cfg.beta1,
-                                                     c->cfg.beta2, c->cfg.eps, (float)bc1, (float)bc2);
+                                                     c->cfg.beta2, c->cfg.eps, c->bc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return refresh_bf16(c);
@@ -740,6 +799,10 @@ cudaError_t adam_update(sur_ctx* c) {
 
 int ensure_rows(sur_ctx* ctx, size_t n) {
   if (n <= ctx->cap_rows) return SUR_OK;
+  // a captured epoch reads the old training-set buffers: drop it
+  if (ctx->epoch_graph) cudaGraphExecDestroy(ctx->epoch_graph);
+  ctx->epoch_graph = nullptr;
+  ctx->graph_n = ctx->graph_batch = 0;
   cudaFree(ctx->xfull);
   cudaFree(ctx->tfull);
   cudaFree(ctx->perm);
@@ -765,7 +828,9 @@ int ensure_scores(sur_ctx* ctx, size_t n) {
 void free_all(sur_ctx* c) {
   void* ptrs[] = {c->p, c->g, c->m, c->v, c->w1b, c->w2b, c->w3b, c->xb, c->h1, c->h2, c->dz2, c->dz1,
                   c->dz2lo, c->dz1lo, c->h1lo, c->h2lo, c->h2f, c->z2f, c->dz1f, c->y, c->dy, c->tb, c->part, c->xfull, c->tfull, c->perm, c->topk_work, c->scores,
-                  c->idx, c->uerr, c->dz2T, c->dz2loT, c->h1T, c->h1loT, c->dz1T, c->dz1loT, c->xT, c->w2T};
+                  c->idx, c->uerr, c->dz2T, c->dz2loT, c->h1T, c->h1loT, c->dz1T, c->dz1loT, c->xT, c->w2T,
+                  c->kpart, c->dstep, c->bc, c->loss_acc};
+  if (c->epoch_graph) cudaGraphExecDestroy(c->epoch_graph);
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -879,6 +944,9 @@ int sur_create(const sur_config* cfg, sur_ctx_t** out) {
             dalloc(&ctx->h1T, (size_t)HID * B) == cudaSuccess && dalloc(&ctx->h1loT, (size_t)HID * B) == cudaSuccess &&
             dalloc(&ctx->dz1T, (size_t)HID * B) == cudaSuccess && dalloc(&ctx->dz1loT, (size_t)HID * B) == cudaSuccess &&
             dalloc(&ctx->xT, (size_t)IN * B) == cudaSuccess && dalloc(&ctx->w2T, (size_t)HID * HID) == cudaSuccess &&
+            dalloc(&ctx->kpart, (size_t)UM_MAXSPLIT * HID * HID) == cudaSuccess &&
+            dalloc(&ctx->dstep, 1) == cudaSuccess && dalloc(&ctx->bc, 2) == cudaSuccess &&
+            dalloc(&ctx->loss_acc, 1) == cudaSuccess && cudaMemset(ctx->dstep, 0, sizeof(long long)) == cudaSuccess &&
             cudaMemset(ctx->uerr, 0, sizeof(int)) == cudaSuccess &&
             cudaFuncSetAttribute(gemm_umma<HID>, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
             cudaFuncSetAttribute(gemm_umma<IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
@@ -929,6 +997,7 @@ int sur_set_params(sur_ctx_t* ctx, const float* params) {
   CK(cudaMemcpyAsync(ctx->p, params, NP * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->m, 0, NP * sizeof(float), ctx->stream));
   CK(cudaMemsetAsync(ctx->v, 0, NP * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->dstep, 0, sizeof(long long), ctx->stream));
   ctx->step = 0;
   ctx->mu = 0.0;
   ctx->sigma = 1.0;
@@ -1048,8 +1117,6 @@ int sur_train(sur_ctx_t* ctx, const float* X, const float* y, int32_t n, int32_t
   CK(cudaMemcpyAsync(ctx->tfull, t.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   std::vector<int> perm(n);
   uint64_t st = ctx->cfg.seed * 0x2545F4914F6CDD1DULL + (uint64_t)ctx->step;
-  const int nblk_max = (batch + 255) / 256;
-  std::vector<float> part(nblk_max);
   double last = 0.0;
   for (int ep = 0; ep < epochs; ++ep) {
     for (int i = 0; i < n; ++i) perm[i] = i;
@@ -1058,22 +1125,52 @@ int sur_train(sur_ctx_t* ctx, const float* X, const float* y, int32_t n, int32_t
       std::swap(perm[i], perm[j]);
     }
     CK(cudaMemcpyAsync(ctx->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    double ep_loss = 0.0;
-    for (int b0 = 0; b0 < n; b0 += batch) {
-      const int nb = std::min(batch, n - b0);
-      gather_rows<<<nb, 128, 0, ctx->stream>>>(ctx->xfull, ctx->tfull, ctx->perm, b0, nb, ctx->xb, ctx->tb);
-      CK(cudaGetLastError());
-      CK(forward_batch(ctx, nb));
-      CK(backward_batch(ctx, nb));
-      CK(adam_update(ctx));
-      if (ep == epochs - 1) {
-        const int nblk = (nb + 255) / 256;
-        CK(cudaMemcpyAsync(part.data(), ctx->part, nblk * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        for (int q = 0; q < nblk; ++q) ep_loss += part[q];
+    // one epoch = one graph launch: every batch's gather, forward, backward,
+    // Adam update and loss partials, captured once per (n, batch)
+    if (!ctx->epoch_graph || ctx->graph_n != n || ctx->graph_batch != batch) {
+      if (ctx->epoch_graph) cudaGraphExecDestroy(ctx->epoch_graph);
+      ctx->epoch_graph = nullptr;
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cudaSuccess;
+      for (int b0 = 0; b0 < n && ce == cudaSuccess; b0 += batch) {
+        const int nb = std::min(batch, n - b0);
+        gather_rows<<<nb, 128, 0, ctx->stream>>>(ctx->xfull, ctx->tfull, ctx->perm, b0, nb, ctx->xb, ctx->tb);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = forward_batch(ctx, nb);
+        if (ce == cudaSuccess) ce = backward_batch(ctx, nb);
+        if (ce == cudaSuccess) ce = adam_update(ctx);
+        if (ce == cudaSuccess) {
+          loss_accumulate<<<1, 1, 0, ctx->stream>>>(ctx->part, (nb + 255) / 256, ctx->loss_acc);
+          ce = cudaGetLastError();
+        }
       }
+      cudaError_t ee = cudaStreamEndCapture(ctx->stream, &gr);
+      if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return fail(ctx, SUR_ECUDA, std::string("sur_train: epoch capture: ") +
+                                        cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+      }
+      cudaError_t ie = cudaGraphInstantiate(&ctx->epoch_graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) {
+        ctx->epoch_graph = nullptr;
+        return fail(ctx, SUR_ECUDA, std::string("sur_train: instantiate: ") + cudaGetErrorString(ie));
+      }
+      ctx->graph_n = n;
+      ctx->graph_batch = batch;
+      // the capture advanced the host mirror of the step count without running
+      ctx->step -= (n + batch - 1) / batch;
     }
-    if (ep == epochs - 1) last = ep_loss / n;
+    CK(cudaMemsetAsync(ctx->loss_acc, 0, sizeof(double), ctx->stream));
+    CK(cudaGraphLaunch(ctx->epoch_graph, ctx->stream));
+    ctx->step += (n + batch - 1) / batch;
+    if (ep == epochs - 1) {
+      double acc = 0.0;
+      CK(cudaMemcpyAsync(&acc, ctx->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      last = acc / n;
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   if (loss_out) *loss_out = (float)last;
