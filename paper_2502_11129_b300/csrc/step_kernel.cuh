@@ -72,6 +72,40 @@ struct __align__(16) WarpSmem {
 static_assert(16 * (sizeof(WarpSmem) + 1024) <= 164 * 1024, "per-warp shared memory");
 
 __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFull, x, src); }
+
+// Double-float arithmetic (Dekker 1971 products, Knuth two-sum): a value is
+// h + l in FP32 with |l| <= ulp(h) / 2, about 44 bits.  The round-to-nearest
+// intrinsics keep the compiler from fusing the error-free steps into FMAs.
+struct f2 {
+  float h, l;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ f2 quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  const f2 s = two_sum(a.h, b.h);
+  return quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ f2 f2_prod(float a, float b) {  // exact
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ f2 f2_mulf(f2 a, float b) {
+  const f2 p = f2_prod(a.h, b);
+  return quick_two_sum(p.h, __fmaf_rn(a.l, b, p.l));
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  const f2 p = f2_prod(a.h, b.h);
+  return quick_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ f2 f2_shf(f2 a, int src) { return {shf(a.h, src), shf(a.l, src)}; }
 __device__ __forceinline__ int shfi(int x, int src) { return __shfl_sync(kFull, x, src); }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -292,35 +326,45 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         }
       }
     }
-    // FP64 height chain for the ground contacts: the third row of R_b and the
-    // frame-origin height relative to O.  A contact's push-out speed is
-    // ERP * depth / dt with depths of ~0.1 mm; heights are evaluated in FP64
-    // (from the FP32 state) so that contact activation is decided in the same
-    // precision as the FP64 reference; everything else stays FP32.
-    double hz0, hz1, hz2, hzb = 0.0;
+    // Height chain for the ground contacts in double-float: the third row of
+    // R_b and the frame-origin height relative to O.  A contact's push-out
+    // speed is ERP * depth / dt with depths of ~0.1 mm, so contact activation
+    // and depth are taken from heights about as exact as the FP64 reference's
+    // (from the FP32 state); everything else stays FP32.
+    f2 hz0, hz1, hz2, hzb = {0.f, 0.f};
     {
-      const double dw = qw, dx = qx, dy = qy, dz = qz;
-      hz0 = 2.0 * (dx * dz - dw * dy);
-      hz1 = 2.0 * (dy * dz + dw * dx);
-      hz2 = 1.0 - 2.0 * (dx * dx + dy * dy);
-      const int k = axis, i = (axis + 1) % 3, j = (axis + 2) % 3;
+      hz0 = f2_add(f2_prod(qx, qz), f2_neg(f2_prod(qw, qy)));
+      hz1 = f2_add(f2_prod(qy, qz), f2_prod(qw, qx));
+      hz0 = {2.f * hz0.h, 2.f * hz0.l};
+      hz1 = {2.f * hz1.h, 2.f * hz1.l};
+      const f2 xy = f2_add(f2_prod(qx, qx), f2_prod(qy, qy));
+      hz2 = f2_add(f2{1.f, 0.f}, f2{-2.f * xy.h, -2.f * xy.l});
+      const f2 cdf = {cth, (float)(cd - (double)cth)}, sdf = {sth, (float)(sd - (double)sth)};
+      const int k = axis;  // columns i = k + 1, j = k + 2 (mod 3) mix
+      // the fixed frame's rows and offset (exact FP32 model values)
+      float Fr[9], Fp[3];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) Fr[t] = fld(F_RFIX + t);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) Fp[t] = fld(F_PFIX + t);
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
-        const double p0 = __shfl_sync(kFull, hz0, par0), p1 = __shfl_sync(kFull, hz1, par0);
-        const double p2 = __shfl_sync(kFull, hz2, par0), pb = __shfl_sync(kFull, hzb, par0);
+        const f2 p0 = f2_shf(hz0, par0), p1 = f2_shf(hz1, par0), p2 = f2_shf(hz2, par0), pb = f2_shf(hzb, par0);
         if (depth == lvl) {
           // (third row of R_parent) x R_fix, then the hinge rotation mixes columns i, j
-          double t[3];
+          f2 t[3];
 #pragma unroll
           for (int col = 0; col < 3; ++col)
-            t[col] = p0 * (double)fld(F_RFIX + col) + p1 * (double)fld(F_RFIX + 3 + col) +
-                     p2 * (double)fld(F_RFIX + 6 + col);
-          const double ti = t[i], tj = t[j];
-          double out[3];
-          out[k] = t[k];
-          out[i] = cd * ti + sd * tj;
-          out[j] = -sd * ti + cd * tj;
-          hz0 = out[0]; hz1 = out[1]; hz2 = out[2];
-          hzb = pb + (p0 * (double)fld(F_PFIX) + p1 * (double)fld(F_PFIX + 1) + p2 * (double)fld(F_PFIX + 2));
+            t[col] = f2_add(f2_add(f2_mulf(p0, Fr[col]), f2_mulf(p1, Fr[3 + col])), f2_mulf(p2, Fr[6 + col]));
+          const f2 ti = k == 0 ? t[1] : (k == 1 ? t[2] : t[0]);
+          const f2 tj = k == 0 ? t[2] : (k == 1 ? t[0] : t[1]);
+          const f2 tk = k == 0 ? t[0] : (k == 1 ? t[1] : t[2]);
+          const f2 oi = f2_add(f2_mul(cdf, ti), f2_mul(sdf, tj));
+          const f2 oj = f2_add(f2_mul(cdf, tj), f2_neg(f2_mul(sdf, ti)));
+          // out[k] = tk, out[i] = oi, out[j] = oj with i = k + 1, j = k + 2 (mod 3)
+          hz0 = k == 0 ? tk : (k == 1 ? oj : oi);
+          hz1 = k == 0 ? oi : (k == 1 ? tk : oj);
+          hz2 = k == 0 ? oj : (k == 1 ? oi : tk);
+          hzb = f2_add(pb, f2_add(f2_add(f2_mulf(p0, Fp[0]), f2_mulf(p1, Fp[1])), f2_mulf(p2, Fp[2])));
         }
       }
     }
@@ -526,15 +570,18 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       const float h0 = sph ? 0.f : hr, h1 = sph ? 0.f : fld(F_HALF + 1), h2 = sph ? 0.f : fld(F_HALF + 2);
       const float drop = sph ? hr : 0.f;
       const float c0 = fld(F_COM), c1 = fld(F_COM + 1), c2 = fld(F_COM + 2);
+      // vertex height p0z + (hzb + hz . l) - drop in double-float
       auto vheight = [&](int k) {
-        const double l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
-        return (double)p0z + (hzb + (hz0 * l0 + hz1 * l1 + hz2 * l2)) - (double)drop;
+        const float l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
+        const f2 hl = f2_add(f2_add(f2_mulf(hz0, l0), f2_mulf(hz1, l1)), f2_mulf(hz2, l2));
+        return f2_add(f2_add(two_sum(p0z, -drop), hzb), hl);
       };
+      auto below = [](f2 h) { return h.h < 0.f || (h.h == 0.f && h.l < 0.f); };
       if (body) {
         const int nvert = sph ? 1 : 8;
 #pragma unroll 1
         for (int k = 0; k < nvert; ++k)
-          if (vheight(k) < 0.0) mask8 |= 1u << k;
+          if (below(vheight(k))) mask8 |= 1u << k;
       }
       const int cnt = __popc(mask8);
       int incl = cnt;
@@ -552,7 +599,10 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 #pragma unroll
         for (int a = 0; a < 3; ++a) pr[a] = r[a] + (R[3 * a] * l0 + R[3 * a + 1] * l1 + R[3 * a + 2] * l2);
         pr[2] -= drop;
-        if (off < kCand) put_candidate(cand, off, pr, up, (float)(-vheight(k)), lane, 255);
+        if (off < kCand) {
+          const f2 vh = vheight(k);
+          put_candidate(cand, off, pr, up, -(vh.h + vh.l), lane, 255);
+        }
         ++off;
       }
       ncand = shfi(incl, 31);

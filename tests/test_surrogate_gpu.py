@@ -89,7 +89,11 @@ def test_gradients_match_oracle():
     assert abs(loss - lr_) <= 1e-2 * lr_
     for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
         rel = np.linalg.norm(gd[k] - gr[k]) / np.linalg.norm(gr[k])
+        # the worst single entry, against the tensor's largest entry
+        worst = np.abs(gd[k] - gr[k]).max() / np.abs(gr[k]).max()
+        print(f"gradient {k}: relative norm error {rel:.3g}, worst entry {worst:.3g} of the largest")
         assert rel <= 2e-2, (k, rel)
+        assert worst <= 2e-2, (k, worst)
     s.close()
 
 
