@@ -368,57 +368,84 @@ __global__ void relu_mask_split(float* __restrict__ dz, const bf16* __restrict__
 }
 
 // column sums over the batch: gb2, gW3 (from dy, W3, H2 in FP32) and gb1
-// (from the FP32 dZ1) per block of 32 columns x 8 batch-row lanes; the last
-// block sums dy for gb3.  Partial sums are combined in a fixed order.
+// (from the FP32 dZ1).  Block (x, y): 32 columns x 8 row lanes over batch
+// slab y (rows y, y + S, ...  with S = gridDim.y slabs, 8 lanes apart); the
+// x = HID / 32 blocks sum dy for gb3.  Each block writes its partial sums;
+// col_sums_finish adds the slabs in a fixed order.
+constexpr int kColSlabs = 16;
 __global__ void col_sums(const float* __restrict__ dy, const bf16* __restrict__ W3, const float* __restrict__ H2,
-                         const float* __restrict__ dZ1, int n, float* grads) {
-  __shared__ float part[3][8][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+                         const float* __restrict__ dZ1, int n, float* __restrict__ part) {
+  __shared__ float acc[3][8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, slab = blockIdx.y, S = gridDim.y;
   float b2 = 0.f, w3 = 0.f, b1 = 0.f;
   if (blockIdx.x < HID / 32) {
     const int j = blockIdx.x * 32 + tx;
     const float w3j = __bfloat162float(W3[j]);
-    for (int m = ty; m < n; m += 8) {
+    for (int m = slab * 8 + ty; m < n; m += 8 * S) {
       const float h = H2[(long)m * HID + j];
       b2 += h > 0.f ? dy[m] * w3j : 0.f;
       w3 += dy[m] * h;
       b1 += dZ1[(long)m * HID + j];
     }
   } else {
-    for (int m = ty * 32 + tx; m < n; m += 256) b2 += dy[m];
+    for (int m = slab * 256 + ty * 32 + tx; m < n; m += 256 * S) b2 += dy[m];
   }
-  part[0][ty][tx] = b2;
-  part[1][ty][tx] = w3;
-  part[2][ty][tx] = b1;
+  acc[0][ty][tx] = b2;
+  acc[1][ty][tx] = w3;
+  acc[2][ty][tx] = b1;
   __syncthreads();
   if (ty != 0) return;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   for (int r = 0; r < 8; ++r) {
-    s0 += part[0][r][tx];
-    s1 += part[1][r][tx];
-    s2 += part[2][r][tx];
+    s0 += acc[0][r][tx];
+    s1 += acc[1][r][tx];
+    s2 += acc[2][r][tx];
   }
-  if (blockIdx.x < HID / 32) {
-    const int j = blockIdx.x * 32 + tx;
-    grads[OB2 + j] = s0;
-    grads[OW3 + j] = s1;
-    grads[OB1 + j] = s2;
+  // partial layout: [slab][3][HID + 32] (the last 32 columns: the dy lanes)
+  float* o = part + (size_t)slab * 3 * (HID + 32);
+  const int c = blockIdx.x * 32 + tx;
+  o[c] = s0;
+  o[(HID + 32) + c] = s1;
+  o[2 * (HID + 32) + c] = s2;
+}
+
+__global__ void col_sums_finish(const float* __restrict__ part, int S, float* __restrict__ grads) {
+  const int c = threadIdx.x;  // HID + 32 threads
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int y = 0; y < S; ++y) {
+    const float* o = part + (size_t)y * 3 * (HID + 32);
+    s0 += o[c];
+    s1 += o[(HID + 32) + c];
+    s2 += o[2 * (HID + 32) + c];
+  }
+  if (c < HID) {
+    grads[OB2 + c] = s0;
+    grads[OW3 + c] = s1;
+    grads[OB1 + c] = s2;
   } else {
-    // the 32 lanes' sums of dy, in lane order
-    float t = 0.f;
-    for (int l = 0; l < 32; ++l) t += __shfl_sync(0xffffffffu, s0, l);
-    if (tx == 0) grads[OB3] = t;
+    // the dy lanes' sums, in lane order, for gb3
+    __shared__ float lanes[32];
+    lanes[c - HID] = s0;
+    __syncwarp();
+    if (c == HID) {
+      float t = 0.f;
+      for (int l = 0; l < 32; ++l) t += lanes[l];
+      grads[OB3] = t;
+    }
   }
 }
 
 // Adam's step count lives on the device (so that a captured training epoch
-// replays with the right bias corrections): advance it and compute
-// 1 - b1^t, 1 - b2^t in FP64, rounded to FP32
-__global__ void adam_prep(long long* step, double b1, double b2, float* bc) {
+// replays with the right bias corrections): advance it and the running
+// powers b1^t, b2^t (FP64 products), and give 1 - b1^t, 1 - b2^t in FP32
+__global__ void adam_prep(long long* step, double* pw, double b1, double b2, float* bc) {
   const long long t = *step + 1;
   *step = t;
-  bc[0] = (float)(1.0 - pow(b1, (double)t));
-  bc[1] = (float)(1.0 - pow(b2, (double)t));
+  const double p1 = (t == 1 ? 1.0 : pw[0]) * b1, p2 = (t == 1 ? 1.0 : pw[1]) * b2;
+  pw[0] = p1;
+  pw[1] = p2;
+  bc[0] = (float)(1.0 - p1);
+  bc[1] = (float)(1.0 - p2);
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -636,6 +663,8 @@ struct sur_ctx {
   int* uerr = nullptr;     // set by gemm_umma when a tensor-core wait gives up
   float* kpart = nullptr;  // split-K partials of the weight gradients (UM_MAXSPLIT x HID x HID)
   long long* dstep = nullptr;  // Adam's step count (device)
+  double* dpow = nullptr;      // b1^t, b2^t
+  float* colpart = nullptr;    // column-sum partials (kColSlabs x 3 x (HID + 32))
   float* bc = nullptr;         // its bias corrections 1 - b1^t, 1 - b2^t
   double* loss_acc = nullptr;  // sum of squared errors of an epoch (device)
   // one captured training epoch (batches of the permuted set), keyed by (n, batch)
@@ -783,13 +812,15 @@ cudaError_t backward_batch(sur_ctx* c, int n) {
   w.Cf = c->g + OW1; w.epi = EPI_F32;
   e = launch_umma<IN>(c, HID, kp, {&c->tm_dz1T, &c->tm_dz1loT}, {&c->tm_xT, &c->tm_xT}, w, UM_MAXSPLIT);
   if (e != cudaSuccess) return e;
-  col_sums<<<HID / 32 + 1, dim3(32, 8), 0, c->stream>>>(c->dy, c->w3b, c->h2f, c->dz1f, n, c->g);
+  col_sums<<<dim3(HID / 32 + 1, kColSlabs), dim3(32, 8), 0, c->stream>>>(c->dy, c->w3b, c->h2f, c->dz1f, n,
+                                                                       c->colpart);
+  col_sums_finish<<<1, HID + 32, 0, c->stream>>>(c->colpart, kColSlabs, c->g);
   return cudaGetLastError();
 }
 
 cudaError_t adam_update(sur_ctx* c) {
   c->step += 1;  // host mirror of the device count
-  adam_prep<<<1, 1, 0, c->stream>>>(c->dstep, (double)c->cfg.beta1, (double)c->cfg.beta2, c->bc);
+  adam_prep<<<1, 1, 0, c->stream>>>(c->dstep, c->dpow, (double)c->cfg.beta1, (double)c->cfg.beta2, c->bc);
   adam_kernel<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->p, c->g, c->m, c->v, NP, c->cfg.lr, c->cfg.beta1,
                                                      c->cfg.beta2, c->cfg.eps, c->bc);
   cudaError_t e = cudaGetLastError();
@@ -829,7 +860,7 @@ void free_all(sur_ctx* c) {
   void* ptrs[] = {c->p, c->g, c->m, c->v, c->w1b, c->w2b, c->w3b, c->xb, c->h1, c->h2, c->dz2, c->dz1,
                   c->dz2lo, c->dz1lo, c->h1lo, c->h2lo, c->h2f, c->z2f, c->dz1f, c->y, c->dy, c->tb, c->part, c->xfull, c->tfull, c->perm, c->topk_work, c->scores,
                   c->idx, c->uerr, c->dz2T, c->dz2loT, c->h1T, c->h1loT, c->dz1T, c->dz1loT, c->xT, c->w2T,
-                  c->kpart, c->dstep, c->bc, c->loss_acc};
+                  c->kpart, c->dstep, c->bc, c->loss_acc, c->dpow, c->colpart};
   if (c->epoch_graph) cudaGraphExecDestroy(c->epoch_graph);
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -946,6 +977,8 @@ int sur_create(const sur_config* cfg, sur_ctx_t** out) {
             dalloc(&ctx->xT, (size_t)IN * B) == cudaSuccess && dalloc(&ctx->w2T, (size_t)HID * HID) == cudaSuccess &&
             dalloc(&ctx->kpart, (size_t)UM_MAXSPLIT * HID * HID) == cudaSuccess &&
             dalloc(&ctx->dstep, 1) == cudaSuccess && dalloc(&ctx->bc, 2) == cudaSuccess &&
+            dalloc(&ctx->dpow, 2) == cudaSuccess &&
+            dalloc(&ctx->colpart, (size_t)kColSlabs * 3 * (HID + 32)) == cudaSuccess &&
             dalloc(&ctx->loss_acc, 1) == cudaSuccess && cudaMemset(ctx->dstep, 0, sizeof(long long)) == cudaSuccess &&
             cudaMemset(ctx->uerr, 0, sizeof(int)) == cudaSuccess &&
             cudaFuncSetAttribute(gemm_umma<HID>, cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM) == cudaSuccess &&
