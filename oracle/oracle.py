@@ -38,9 +38,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
 
-MAXB = 32
-MAXV = 38
-MAXQ = 39
+MAXB = 64
+MAXV = 70
+MAXQ = 71
 MAXCAND = 4096
 NPHASE = 9
 PHASES = ["cpg", "fk", "rnea", "crba", "chol", "contact", "jac", "pgs", "integ"]
@@ -51,7 +51,7 @@ class Model(C.Structure):
     _fields_ = [
         ("nb", C.c_int32), ("root_fixed", C.c_int32),
         ("parent", C.c_int32 * MAXB), ("axis", C.c_int32 * MAXB),
-        ("exclude", C.c_uint32 * MAXB),
+        ("exclude", C.c_uint64 * MAXB),
         ("R_fix", (C.c_double * 9) * MAXB), ("p_fix", (C.c_double * 3) * MAXB),
         ("half", (C.c_double * 3) * MAXB), ("com", (C.c_double * 3) * MAXB),
         ("mass", C.c_double * MAXB), ("w_int", C.c_double * MAXB),
@@ -155,7 +155,7 @@ def model_from_population(pop, i: int) -> Model:
     nb = int(pop.nb[i])
     m.nb = nb
     m.root_fixed = 0
-    for b in range(MAXB):
+    for b in range(min(MAXB, pop.parent.shape[1])):
         m.parent[b] = int(pop.parent[i, b])
         m.axis[b] = int(pop.axis[i, b])
         m.exclude[b] = int(pop.exclude[i, b])

@@ -27,7 +27,7 @@ class Model32(C.Structure):
     _fields_ = [
         ("nb", C.c_int32), ("root_fixed", C.c_int32),
         ("parent", C.c_int32 * O.MAXB), ("axis", C.c_int32 * O.MAXB),
-        ("exclude", C.c_uint32 * O.MAXB),
+        ("exclude", C.c_uint64 * O.MAXB),
         ("R_fix", (F * 9) * O.MAXB), ("p_fix", (F * 3) * O.MAXB),
         ("half", (F * 3) * O.MAXB), ("com", (F * 3) * O.MAXB),
         ("mass", F * O.MAXB), ("w_int", F * O.MAXB), ("w_cpl", F * O.MAXB),

@@ -30,9 +30,9 @@
 #define ORC_H
 #include <stdint.h>
 
-#define ORC_MAXB 32
-#define ORC_MAXV 38
-#define ORC_MAXQ 39
+#define ORC_MAXB 64
+#define ORC_MAXV 70
+#define ORC_MAXQ 71
 #define ORC_MAXCAND 4096
 #define ORC_CAPMAX 128
 #define ORC_NPHASE 9
@@ -57,11 +57,11 @@ enum { ORC_GEOM_BOX = 0, ORC_GEOM_SPHERE = 1 };
 typedef ORC_REAL real;
 
 typedef struct {
-    int32_t nb;                 /* bodies, 1..32; body 0 is the root        */
+    int32_t nb;                 /* bodies, 1..64; body 0 is the root        */
     int32_t root_fixed;         /* 1: root pinned at (root_R, root_p)       */
     int32_t parent[ORC_MAXB];   /* parent[b] < b for b >= 1                 */
     int32_t axis[ORC_MAXB];     /* hinge axis index (0,1,2) in child frame  */
-    uint32_t exclude[ORC_MAXB]; /* bit j: body never collides with body j   */
+    uint64_t exclude[ORC_MAXB]; /* bit j: body never collides with body j   */
     real R_fix[ORC_MAXB][9];  /* child frame at zero angle, in parent     */
     real p_fix[ORC_MAXB][3];
     real half[ORC_MAXB][3];   /* box half extents (body axes)             */

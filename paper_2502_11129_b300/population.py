@@ -43,7 +43,8 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-MAXB = 32                 # padded body slots per robot
+MAXB = 32                 # padded body slots per robot (default)
+MAXB_LONG = 64            # slots of populations with chains beyond 32 bodies
 MAX_HINGES = 20
 CORE_HALF_MM = 50
 BRICK_HALF_MM = 30
@@ -77,7 +78,8 @@ def _rot_x_quarter(r: int) -> np.ndarray:
 class Population:
     """Padded per-robot model description plus initial state.
 
-    Arrays are indexed [robot, body] with MAXB body slots.  Units are SI
+    Arrays are indexed [robot, body] with ``slots`` body slots (MAXB, or
+    MAXB_LONG for chains of more than 32 bodies).  Units are SI
     (metres, kilograms, radians).  Hinge i of a robot is body i+1.
     """
     kind: str
@@ -94,10 +96,14 @@ class Population:
     w_cpl: np.ndarray         # (n, MAXB) float64 CPG coupling to the parent hinge
     q0: np.ndarray            # (n, MAXB+8) float64, first nq entries used
     v0: np.ndarray            # (n, MAXB+8) float64, first nv entries used
-    exclude: np.ndarray       # (n, MAXB) uint32 bit j set: no contact with body j
+    exclude: np.ndarray       # (n, MAXB) uint64 bit j set: no contact with body j
     genome_face: np.ndarray   # (n, MAXB) int8 face of the parent each brick sits on
     genome_rot: np.ndarray    # (n, MAXB) int8 quarter-turn rotation of each brick
     geom: np.ndarray          # (n, MAXB) int8 GEOM_BOX, or GEOM_SPHERE (radius half[..., 0])
+
+    @property
+    def slots(self) -> int:
+        return int(self.parent.shape[1])
 
     @property
     def nq(self) -> np.ndarray:
@@ -132,25 +138,25 @@ class Population:
         return Population(**fields)
 
 
-def _empty(kind: str, n: int) -> Population:
+def _empty(kind: str, n: int, slots: int = MAXB) -> Population:
     return Population(
         kind=kind, n=n,
         nb=np.zeros(n, np.int32),
-        parent=np.full((n, MAXB), -1, np.int8),
-        axis=np.zeros((n, MAXB), np.int8),
-        R_fix=np.tile(np.eye(3).reshape(1, 1, 9), (n, MAXB, 1)),
-        p_fix=np.zeros((n, MAXB, 3)),
-        half=np.zeros((n, MAXB, 3)),
-        com=np.zeros((n, MAXB, 3)),
-        mass=np.zeros((n, MAXB)),
-        w_int=np.zeros((n, MAXB)),
-        w_cpl=np.zeros((n, MAXB)),
-        q0=np.zeros((n, MAXB + 8)),
-        v0=np.zeros((n, MAXB + 8)),
-        exclude=np.zeros((n, MAXB), np.uint32),
-        genome_face=np.full((n, MAXB), -1, np.int8),
-        genome_rot=np.zeros((n, MAXB), np.int8),
-        geom=np.zeros((n, MAXB), np.int8),
+        parent=np.full((n, slots), -1, np.int8),
+        axis=np.zeros((n, slots), np.int8),
+        R_fix=np.tile(np.eye(3).reshape(1, 1, 9), (n, slots, 1)),
+        p_fix=np.zeros((n, slots, 3)),
+        half=np.zeros((n, slots, 3)),
+        com=np.zeros((n, slots, 3)),
+        mass=np.zeros((n, slots)),
+        w_int=np.zeros((n, slots)),
+        w_cpl=np.zeros((n, slots)),
+        q0=np.zeros((n, slots + 8)),
+        v0=np.zeros((n, slots + 8)),
+        exclude=np.zeros((n, slots), np.uint64),
+        genome_face=np.full((n, slots), -1, np.int8),
+        genome_rot=np.zeros((n, slots), np.int8),
+        geom=np.zeros((n, slots), np.int8),
     )
 
 
@@ -263,8 +269,8 @@ def _write_robot(pop: Population, i: int, lat: _Lattice, rng, quad_weights=None)
         pop.genome_face[i, b] = lat.face[b]
         pop.genome_rot[i, b] = lat.rot[b]
     for a, b in lat.touching_pairs():
-        pop.exclude[i, a] |= np.uint32(1 << b)
-        pop.exclude[i, b] |= np.uint32(1 << a)
+        pop.exclude[i, a] |= np.uint64(1 << b)
+        pop.exclude[i, b] |= np.uint64(1 << a)
     w_int = rng.uniform(-1.0, 1.0, size=nb)
     w_cpl = rng.uniform(-1.0, 1.0, size=nb)
     for b in range(1, nb):
@@ -394,15 +400,17 @@ def rope_lattice(links: int) -> _Lattice:
 
 
 def rope(n: int, seed: int = 5, links: int = 25) -> Population:
-    """A long chain (up to 25 links, the per-robot body bound): a core cube
-    trailing a chain of bricks, dropped from U[0, 0.3] m above its resting
-    height, bent in the horizontal plane (vertical-axis hinges U[-0.3, 0.3],
-    the others straight), hinge rates N(0, 1).  Run with actuate=0 the chain
-    is passive (a rope); with the CPG on it is a snake."""
-    if not 1 <= links <= 25:
-        raise ValueError("links must be in 1..25")
+    """A long chain (up to 63 links, the per-robot body bound of 64): a core
+    cube trailing a chain of bricks, dropped from U[0, 0.3] m above its
+    resting height, bent in the horizontal plane (vertical-axis hinges
+    U[-0.3, 0.3], the others straight), hinge rates N(0, 1).  Run with
+    actuate=0 the chain is passive (a rope); with the CPG on it is a snake.
+    Chains of more than 25 links (more than 31 dofs) take the simulator's
+    block-per-robot path; more than 31 links need MAXB_LONG body slots."""
+    if not 1 <= links <= MAXB_LONG - 1:
+        raise ValueError(f"links must be in 1..{MAXB_LONG - 1}")
     rng = np.random.default_rng(seed)
-    pop = _empty("rope", n)
+    pop = _empty("rope", n, MAXB if links + 1 <= MAXB else MAXB_LONG)
     lat = rope_lattice(links)
     vertical = np.array([k % 2 == 1 for k in range(links)])  # quarter-turned links
     for i in range(n):
@@ -411,6 +419,38 @@ def rope(n: int, seed: int = 5, links: int = 25) -> Population:
         pop.q0[i, 7:7 + links] = np.where(vertical, rng.uniform(-0.3, 0.3, size=links), 0.0)
         pop.v0[i, 6:6 + links] = rng.normal(0.0, 1.0, size=links)
     return pop
+
+
+def concat(pops) -> Population:
+    """One population of several (kind of the first): body-slot arrays are
+    padded to the largest slot count (unused slots as _empty leaves them)."""
+    pops = list(pops)
+    slots = max(p.slots for p in pops)
+    pad_value = {"parent": -1, "genome_face": -1}
+    fields = {}
+    for f in dataclasses.fields(Population):
+        vals = [getattr(p, f.name) for p in pops]
+        if not isinstance(vals[0], np.ndarray):
+            fields[f.name] = vals[0]
+            continue
+        if f.name == "nb":
+            fields[f.name] = np.concatenate(vals)
+            continue
+        out = []
+        for p, x in zip(pops, vals):
+            extra = slots - p.slots
+            if extra:
+                widths = [(0, 0)] * x.ndim
+                widths[1] = (0, extra)
+                if f.name == "R_fix":
+                    eye = np.tile(np.eye(3).reshape(1, 1, 9), (x.shape[0], extra, 1))
+                    x = np.concatenate([x, eye], axis=1)
+                else:
+                    x = np.pad(x, widths, constant_values=pad_value.get(f.name, 0))
+            out.append(x)
+        fields[f.name] = np.concatenate(out)
+    fields["n"] = int(sum(p.n for p in pops))
+    return Population(**fields)
 
 
 def lift(pop: Population, dz: float) -> Population:
@@ -430,7 +470,7 @@ def random_state(pop: Population, seed: int, angle=0.6, rate=1.0, lin=0.5, ang=0
     rng = np.random.default_rng(seed)
     q = pop.q0.copy()
     v = np.zeros_like(pop.v0)
-    s = np.zeros((pop.n, 2 * (MAXB - 1)))
+    s = np.zeros((pop.n, 2 * (pop.slots - 1)))
     for i in range(pop.n):
         nb = int(pop.nb[i])
         quat = rng.normal(size=4)
@@ -446,7 +486,7 @@ def random_state(pop: Population, seed: int, angle=0.6, rate=1.0, lin=0.5, ang=0
 
 def cpg_initial(pop: Population) -> np.ndarray:
     """Initial oscillator state: x = y = 1/sqrt(2) for every hinge."""
-    s = np.zeros((pop.n, 2 * (MAXB - 1)))
+    s = np.zeros((pop.n, 2 * (pop.slots - 1)))
     for i in range(pop.n):
         nh = int(pop.nb[i]) - 1
         s[i, : 2 * nh] = np.sqrt(0.5)
