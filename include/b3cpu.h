@@ -42,8 +42,10 @@ typedef struct cpu_ctx cpu_ctx_t;
 int cpu_create(const sim_config* cfg, int32_t threads, cpu_ctx_t** out);
 int cpu_destroy(cpu_ctx_t* ctx);
 
-/* Replace the population (n >= 1; validated as sim_set_population does).
- * The state is reset to zero and must be set before stepping. */
+/* Replace the population (n >= 1; validated as sim_set_population does, but
+ * with at most SIM_WARP_MAX_BODIES bodies per variant: longer chains are
+ * stepped by the GPU simulator only).  The state is reset to zero and must be
+ * set before stepping. */
 int cpu_set_population(cpu_ctx_t* ctx, const sim_variant_desc* v, int32_t n);
 
 /* State rows of variants [first, first + count) (cpg may be NULL: kept);

@@ -38,6 +38,16 @@
  * Host state arrays use fixed row strides SIM_QW, SIM_VW, SIM_SW floats per
  * variant; unused tail entries are ignored on input and zero on output.
  *
+ * Execution.  Variants of up to SIM_WARP_MAX_BODIES bodies are stepped one
+ * warp each (lane = body / dof / contact row / body pair), variants that are
+ * one free body one thread each, and larger variants (long chains, nv > 31)
+ * one block of two warps each: the tree passes, the Cholesky rows, contact
+ * generation and the contact rows are split over the block's 64 threads
+ * with block barriers at the phase boundaries, and the triangular solves and
+ * the Gauss-Seidel sweep run on one warp (each lane holding up to three
+ * dofs), as they are sequential in their pivots and contacts.  All three
+ * take the same steps in the same order.
+ *
  * Ownership.  All device memory is owned by the context.  Every host
  * pointer is owned by the caller and only read (or written) during the
  * call.  Nothing crosses the ABI as an exception; every entry point returns
@@ -57,12 +67,19 @@ extern "C" {
 
 typedef struct sim_ctx sim_ctx_t;   /* opaque context                       */
 
-#define SIM_MAX_BODIES 26   /* core + up to 25 hinged bricks              */
-#define SIM_QW 32           /* host row stride of q                        */
-#define SIM_VW 32           /* host row stride of v                        */
-#define SIM_SW 64           /* host row stride of the CPG state            */
+#define SIM_MAX_BODIES 64   /* core + up to 63 hinged bodies              */
+#define SIM_WARP_MAX_BODIES 26  /* up to here (nv <= 31) a variant is stepped
+                               by one warp; larger ones (up to 64 bodies,
+                               nv <= 69: long chains) by a block of two
+                               warps, see "Execution" above             */
+#define SIM_QW 72           /* host row stride of q  (nq <= 70)            */
+#define SIM_VW 72           /* host row stride of v  (nv <= 69)            */
+#define SIM_SW 128          /* host row stride of the CPG state (<= 126)   */
 #define SIM_MAX_CONTACT_CAP 64
-#define SIM_MAX_CANDIDATES 256
+#define SIM_MAX_CANDIDATES 256       /* contact candidates per step ...      */
+#define SIM_MAX_CANDIDATES_CHAIN 512 /* ... and for variants of more than
+                                        SIM_WARP_MAX_BODIES bodies (8 vertices
+                                        of 64 boxes)                         */
 
 typedef enum {
     SIM_OK = 0,
@@ -76,7 +93,8 @@ typedef enum {
 #define SIM_ST_NONFINITE 1u        /* state became non-finite: frozen      */
 #define SIM_ST_OVERFLOW 2u         /* more contacts than contact_cap       */
 #define SIM_ST_CHOL 4u             /* non-positive Cholesky pivot: frozen  */
-#define SIM_ST_CANDIDATES 8u       /* more than SIM_MAX_CANDIDATES contact
+#define SIM_ST_CANDIDATES 8u       /* more than SIM_MAX_CANDIDATES (or
+                                      SIM_MAX_CANDIDATES_CHAIN) contact
                                       candidates; the extra were dropped    */
 
 typedef struct {
@@ -119,7 +137,7 @@ typedef struct {
     int32_t n_bodies;             /* 1..SIM_MAX_BODIES                        */
     const int8_t* parent;         /* parent body, -1 for body 0               */
     const int8_t* hinge_axis;     /* hinge axis index 0..2 in the body frame  */
-    const uint32_t* exclude;      /* bit j: body never collides with body j   */
+    const uint64_t* exclude;      /* bit j: body never collides with body j   */
     const float* joint_frame;     /* 12 per body: R (3x3 row-major), p (3):
                                      body frame at zero angle in its parent  */
     const float* half_size;       /* 3 per body: box half extents [m]; a
@@ -271,6 +289,8 @@ int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
  *   - All calls share the one scratch array, which keeps the last call's
  *     contents; calls whose work overlaps on the GPU (other streams, other
  *     host threads) race on it and must be serialised by the caller.
+ *   - Variants have at most SIM_WARP_MAX_BODIES bodies (the layout below has
+ *     32 body slots); longer chains need a context (sim_set_population).
  *   - Every variant is stepped by the general warp-per-robot step kernel of
  *     sim_step_n, in the order given (no size sorting).  Variants that are a
  *     single free body take that general kernel here too, not the

@@ -19,7 +19,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 LIBS = {
-    "libb3sim.so": (["b3sim.cu"], ["step_kernel.cuh", "step_common.cuh", "free_body.cuh", "model_pack.h"], "b3sim.h"),
+    "libb3sim.so": (["b3sim.cu", "chain.cu"], ["step_kernel.cuh", "step_common.cuh", "free_body.cuh", "model_pack.h",
+                                               "chain_kernel.cuh", "chain_layout.h"], "b3sim.h"),
     "libb3sur.so": (["b3sur.cu"], [], "b3sur.h"),
     "libb3cpu.so": (["b3cpu.cu"], ["step_common.cuh", "free_body.cuh", "model_pack.h"], "b3cpu.h"),
 }

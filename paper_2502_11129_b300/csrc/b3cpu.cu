@@ -570,7 +570,9 @@ int cpu_destroy(cpu_ctx_t* ctx) {
 
 int cpu_set_population(cpu_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
   if (!ctx) return SIM_EINVAL;
-  const std::string why = validate_population(v, n, "cpu_set_population");
+  // robots of up to SIM_WARP_MAX_BODIES bodies (the warp layout); longer
+  // chains are stepped by the GPU simulator only
+  const std::string why = validate_population(v, n, "cpu_set_population", SIM_WARP_MAX_BODIES);
   if (!why.empty()) return fail(ctx, SIM_EINVAL, why);
   try {
     pack_population(v, n, ctx->pk);
@@ -596,9 +598,10 @@ int cpu_set_state(cpu_ctx_t* ctx, int32_t first, int32_t count, const float* q, 
     return fail(ctx, SIM_EINVAL, "cpu_set_state: bad range or NULL q/v");
   for (int i = 0; i < count; ++i) {
     const int d = ctx->pk.inv[first + i];
-    std::memcpy(&ctx->q[(size_t)d * 32], q + (size_t)i * SIM_QW, SIM_QW * sizeof(float));
-    std::memcpy(&ctx->v[(size_t)d * 32], v + (size_t)i * SIM_VW, SIM_VW * sizeof(float));
-    if (cpg) std::memcpy(&ctx->s[(size_t)d * 64], cpg + (size_t)i * SIM_SW, SIM_SW * sizeof(float));
+    // rows of the warp layout: nq, nv <= 32, 2 nh <= 64 (the rest of a host row is ignored)
+    std::memcpy(&ctx->q[(size_t)d * 32], q + (size_t)i * SIM_QW, 32 * sizeof(float));
+    std::memcpy(&ctx->v[(size_t)d * 32], v + (size_t)i * SIM_VW, 32 * sizeof(float));
+    if (cpg) std::memcpy(&ctx->s[(size_t)d * 64], cpg + (size_t)i * SIM_SW, 64 * sizeof(float));
     ctx->fit0[2 * d] = q[(size_t)i * SIM_QW];
     ctx->fit0[2 * d + 1] = q[(size_t)i * SIM_QW + 1];
     ctx->status[d] = 0u;
@@ -656,9 +659,18 @@ int cpu_read_state(cpu_ctx_t* ctx, int32_t first, int32_t count, float* q, float
   if (first < 0 || count < 0 || first + count > ctx->n) return fail(ctx, SIM_EINVAL, "cpu_read_state: bad range");
   for (int i = 0; i < count; ++i) {
     const int d = ctx->pk.inv[first + i];
-    if (q) std::memcpy(q + (size_t)i * SIM_QW, &ctx->q[(size_t)d * 32], SIM_QW * sizeof(float));
-    if (v) std::memcpy(v + (size_t)i * SIM_VW, &ctx->v[(size_t)d * 32], SIM_VW * sizeof(float));
-    if (cpg) std::memcpy(cpg + (size_t)i * SIM_SW, &ctx->s[(size_t)d * 64], SIM_SW * sizeof(float));
+    if (q) {
+      std::memcpy(q + (size_t)i * SIM_QW, &ctx->q[(size_t)d * 32], 32 * sizeof(float));
+      std::memset(q + (size_t)i * SIM_QW + 32, 0, (SIM_QW - 32) * sizeof(float));
+    }
+    if (v) {
+      std::memcpy(v + (size_t)i * SIM_VW, &ctx->v[(size_t)d * 32], 32 * sizeof(float));
+      std::memset(v + (size_t)i * SIM_VW + 32, 0, (SIM_VW - 32) * sizeof(float));
+    }
+    if (cpg) {
+      std::memcpy(cpg + (size_t)i * SIM_SW, &ctx->s[(size_t)d * 64], 64 * sizeof(float));
+      std::memset(cpg + (size_t)i * SIM_SW + 64, 0, (SIM_SW - 64) * sizeof(float));
+    }
     if (status) status[i] = ctx->status[d];
   }
   return SIM_OK;

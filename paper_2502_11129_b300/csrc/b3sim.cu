@@ -3,11 +3,13 @@
 // The library owns every device buffer.  A population is packed once into a
 // structure-of-arrays model (per variant: [field][32 body slots]), sorted by
 // robot size, with the robots that are one free body (centred on their frame
-// origin) last.  Steps run as persistent launches of step_kernel (one warp
-// per robot, many steps per launch, slowest robots first) and of
-// free_body_kernel for the single free bodies (one thread per robot); the
-// launch sequence for a given step count is captured once in a CUDA graph and
-// replayed.
+// origin) after them, and robots larger than one warp (long chains) last, in
+// a layout of their own (64 body slots).  Steps run as persistent launches of
+// chain_kernel for the long chains (one block of two warps per robot), of
+// step_kernel (one warp per robot, many steps per launch, slowest robots
+// first) and of free_body_kernel for the single free bodies (one thread per
+// robot); the launch sequence for a given step count is captured once in a
+// CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +25,7 @@
 #include <vector>
 
 #include "b3sim.h"
+#include "chain_layout.h"
 #include "free_body.cuh"
 #include "model_pack.h"
 #include "step_kernel.cuh"
@@ -38,7 +41,8 @@ struct sim_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int n = 0;
-  int n_free = 0;         // single free bodies, the last packed robots (one-body step)
+  int n_free = 0;         // single free bodies, packed after the warp robots (one-body step)
+  int n_chain = 0;        // long chains, the last packed robots (chain layout)
   std::vector<int> perm;  // packed index -> caller index
   std::vector<int> inv;   // caller index -> packed index
   float* d_mf = nullptr;
@@ -58,6 +62,17 @@ struct sim_ctx {
   unsigned* d_order_hist = nullptr;  // cost-bucket counts and cursors (2 x kCostBuckets)
   float* d_stage = nullptr;  // caller-order staging: q | v | s rows
   unsigned* d_stage_st = nullptr;
+  // long chains (packed n - n_chain .. n - 1): model, state rows with the
+  // host strides, scratch
+  float* d_cmf = nullptr;
+  int* d_cmi = nullptr;
+  unsigned long long* d_cmask = nullptr;
+  int4* d_cmeta = nullptr;
+  uint16_t* d_cpairs = nullptr;
+  float* d_cq = nullptr;
+  float* d_cv = nullptr;
+  float* d_cs = nullptr;
+  float* d_cscratch = nullptr;
   StepParams P{};
   // Steps per persistent launch.  A launch lasts as long as its slowest
   // robot, and which robot is slowest changes as contacts come and go, so a
@@ -119,51 +134,88 @@ void free_population(sim_ctx* ctx) {
   dfree(ctx->d_order_hist);
   dfree(ctx->d_stage);
   dfree(ctx->d_stage_st);
+  dfree(ctx->d_cmf);
+  dfree(ctx->d_cmi);
+  dfree(ctx->d_cmask);
+  dfree(ctx->d_cmeta);
+  dfree(ctx->d_cpairs);
+  dfree(ctx->d_cq);
+  dfree(ctx->d_cv);
+  dfree(ctx->d_cs);
+  dfree(ctx->d_cscratch);
   ctx->n = 0;
+  ctx->n_chain = 0;
   ctx->perm.clear();
   ctx->inv.clear();
 }
 
-// caller rows -> packed rows (+ fitness origin, status reset)
+// Packed state rows: robots [0, n_short) in the warp layout (q, v rows of 32
+// floats, CPG rows of 64), long chains [n_short, n) in rows with the host
+// strides (cq, cv, cs).
+struct StateRows {
+  float* q;
+  float* v;
+  float* s;
+  float* cq;
+  float* cv;
+  float* cs;
+  int n_short;
+};
+
+// caller rows -> packed rows (+ fitness origin, status reset); 128 threads
 __global__ void scatter_state(const float* __restrict__ sq, const float* __restrict__ sv,
                               const float* __restrict__ ss, const int* __restrict__ inv_first, int first,
-                              int count, int with_cpg, float* q, float* v, float* s, float* fit0,
-                              unsigned* status) {
+                              int count, int with_cpg, StateRows d, float* fit0, unsigned* status) {
   int i = blockIdx.x;
   if (i >= count) return;
-  int d = inv_first[first + i];
-  int t = threadIdx.x;
-  if (t < SIM_QW) q[(size_t)d * 32 + t] = sq[(size_t)i * SIM_QW + t];
-  if (t < SIM_VW) v[(size_t)d * 32 + t] = sv[(size_t)i * SIM_VW + t];
-  if (with_cpg && t < SIM_SW) s[(size_t)d * 64 + t] = ss[(size_t)i * SIM_SW + t];
+  const int p = inv_first[first + i];
+  const int t = threadIdx.x;
+  if (p < d.n_short) {
+    if (t < 32) d.q[(size_t)p * 32 + t] = sq[(size_t)i * SIM_QW + t];
+    if (t < 32) d.v[(size_t)p * 32 + t] = sv[(size_t)i * SIM_VW + t];
+    if (with_cpg && t < 64) d.s[(size_t)p * 64 + t] = ss[(size_t)i * SIM_SW + t];
+  } else {
+    const size_t c = (size_t)(p - d.n_short);
+    if (t < SIM_QW) d.cq[c * SIM_QW + t] = sq[(size_t)i * SIM_QW + t];
+    if (t < SIM_VW) d.cv[c * SIM_VW + t] = sv[(size_t)i * SIM_VW + t];
+    if (with_cpg && t < SIM_SW) d.cs[c * SIM_SW + t] = ss[(size_t)i * SIM_SW + t];
+  }
   if (t == 0) {
-    fit0[2 * d] = sq[(size_t)i * SIM_QW];
-    fit0[2 * d + 1] = sq[(size_t)i * SIM_QW + 1];
-    status[d] = 0u;
+    fit0[2 * p] = sq[(size_t)i * SIM_QW];
+    fit0[2 * p + 1] = sq[(size_t)i * SIM_QW + 1];
+    status[p] = 0u;
   }
 }
 
-// packed rows -> caller rows
-__global__ void gather_state(const float* __restrict__ q, const float* __restrict__ v, const float* __restrict__ s,
-                             const unsigned* __restrict__ status, const int* __restrict__ inv_first, int first,
-                             int count, float* dq, float* dv, float* ds, unsigned* dst) {
+// packed rows -> caller rows (tails past the warp layout's rows are zero); 128 threads
+__global__ void gather_state(StateRows d, const unsigned* __restrict__ status, const int* __restrict__ inv_first,
+                             int first, int count, float* dq, float* dv, float* ds, unsigned* dst) {
   int i = blockIdx.x;
   if (i >= count) return;
-  int d = inv_first[first + i];
-  int t = threadIdx.x;
-  if (t < SIM_QW) dq[(size_t)i * SIM_QW + t] = q[(size_t)d * 32 + t];
-  if (t < SIM_VW) dv[(size_t)i * SIM_VW + t] = v[(size_t)d * 32 + t];
-  if (t < SIM_SW) ds[(size_t)i * SIM_SW + t] = s[(size_t)d * 64 + t];
-  if (t == 0) dst[i] = status[d];
+  const int p = inv_first[first + i];
+  const int t = threadIdx.x;
+  if (p < d.n_short) {
+    if (t < SIM_QW) dq[(size_t)i * SIM_QW + t] = t < 32 ? d.q[(size_t)p * 32 + t] : 0.f;
+    if (t < SIM_VW) dv[(size_t)i * SIM_VW + t] = t < 32 ? d.v[(size_t)p * 32 + t] : 0.f;
+    if (t < SIM_SW) ds[(size_t)i * SIM_SW + t] = t < 64 ? d.s[(size_t)p * 64 + t] : 0.f;
+  } else {
+    const size_t c = (size_t)(p - d.n_short);
+    if (t < SIM_QW) dq[(size_t)i * SIM_QW + t] = d.cq[c * SIM_QW + t];
+    if (t < SIM_VW) dv[(size_t)i * SIM_VW + t] = d.cv[c * SIM_VW + t];
+    if (t < SIM_SW) ds[(size_t)i * SIM_SW + t] = d.cs[c * SIM_SW + t];
+  }
+  if (t == 0) dst[i] = status[p];
 }
+static_assert(SIM_SW <= 128 && SIM_QW <= 128 && SIM_VW <= 128, "scatter/gather run 128 threads per row");
 
-__global__ void fitness_kernel(const float* __restrict__ q, const float* __restrict__ fit0,
-                               const int* __restrict__ inv, int n, float* out) {
+__global__ void fitness_kernel(StateRows d, const float* __restrict__ fit0, const int* __restrict__ inv, int n,
+                               float* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int d = inv[i];
-  float dx = q[(size_t)d * 32] - fit0[2 * d];
-  float dy = q[(size_t)d * 32 + 1] - fit0[2 * d + 1];
+  const int p = inv[i];
+  const float* q = p < d.n_short ? d.q + (size_t)p * 32 : d.cq + (size_t)(p - d.n_short) * SIM_QW;
+  float dx = q[0] - fit0[2 * p];
+  float dy = q[1] - fit0[2 * p + 1];
   out[i] = sqrtf(dx * dx + dy * dy);
 }
 
@@ -187,7 +239,37 @@ struct LaunchArgs {
   StepParams P;
   cudaStream_t stream;
   int n_free;          // single free bodies after them: packed [n, n + n_free)
+  // long chains: packed [n + n_free, n + n_free + n_chain), model and state
+  // in the chain layout; status, counters and last_nc indexed by packed index
+  int n_chain;
+  const float* cmf;
+  const int* cmi;
+  const unsigned long long* cmask;
+  const int4* cmeta;
+  const uint16_t* cpairs;
+  float* cq;
+  float* cv;
+  float* cs;
+  float* cscratch;
 };
+
+}  // namespace
+
+namespace b3 {
+// chain.cu
+cudaError_t launch_chain(const ChainLaunch& a, int nsteps, const StepParams& P, cudaStream_t stream);
+}
+
+namespace {
+
+// Long chains, one block of two warps per robot (chain_kernel.cuh, launched
+// from its own translation unit).
+cudaError_t launch_chains(const LaunchArgs& a, int nsteps) {
+  const int first = a.n + a.n_free;
+  const b3::ChainLaunch c{a.cmf,    a.cmi,      a.cmask,        a.cmeta,   a.cpairs,           a.cq, a.cv,
+                          a.cs,     a.status + first, a.counters + first, a.cscratch, a.lastnc + first, a.n_chain};
+  return b3::launch_chain(c, nsteps, a.P, a.stream);
+}
 
 // One thread per single free body (a box or a sphere whose centre is its
 // frame origin): the one-body closed form of the step (free_body.cuh) for
@@ -389,6 +471,10 @@ cudaError_t launch_chunk(const LaunchArgs& a, int nsteps, int wpb, bool lock, in
 cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool lock, int wpsm, int spl) {
   for (int done = 0; done < n_steps; done += spl) {
     const int chunk = std::min(spl, n_steps - done);
+    if (a.n_chain > 0) {
+      cudaError_t e = launch_chains(a, chunk);
+      if (e != cudaSuccess) return e;
+    }
     if (a.n > 0) {
       if (a.order) {
         cudaError_t e = cost_order(a);
@@ -409,14 +495,23 @@ cudaError_t enqueue_launches(const LaunchArgs& a, int n_steps, int wpb, bool loc
 }
 
 LaunchArgs ctx_args(sim_ctx* ctx) {
-  return LaunchArgs{ctx->d_mf,     ctx->d_mi,    ctx->d_meta,   ctx->d_pairs,       ctx->d_q,
-                    ctx->d_v,      ctx->d_s,     ctx->d_status, ctx->d_counters,    ctx->d_scratch,
-                    ctx->d_lastnc, ctx->d_order, ctx->d_order_hist, ctx->n - ctx->n_free, ctx->P, ctx->stream,
-                    ctx->n_free};
+  return LaunchArgs{ctx->d_mf,     ctx->d_mi,     ctx->d_meta,   ctx->d_pairs,
+                    ctx->d_q,      ctx->d_v,      ctx->d_s,      ctx->d_status,
+                    ctx->d_counters, ctx->d_scratch, ctx->d_lastnc, ctx->d_order,
+                    ctx->d_order_hist, ctx->n - ctx->n_free - ctx->n_chain, ctx->P, ctx->stream,
+                    ctx->n_free,   ctx->n_chain,  ctx->d_cmf,    ctx->d_cmi,
+                    ctx->d_cmask,  ctx->d_cmeta,  ctx->d_cpairs, ctx->d_cq,
+                    ctx->d_cv,     ctx->d_cs,     ctx->d_cscratch};
 }
 
-cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int wpsm, int spl) {
-  return enqueue_launches(ctx_args(ctx), n_steps, wpb, lock, wpsm, spl);
+StateRows ctx_rows(sim_ctx* ctx) {
+  return StateRows{ctx->d_q, ctx->d_v, ctx->d_s, ctx->d_cq, ctx->d_cv, ctx->d_cs, ctx->n - ctx->n_chain};
+}
+
+cudaError_t enqueue_steps(sim_ctx* ctx, int n_steps, int wpb, bool lock, int wpsm, int spl, bool chains = true) {
+  LaunchArgs a = ctx_args(ctx);
+  if (!chains) a.n_chain = 0;
+  return enqueue_launches(a, n_steps, wpb, lock, wpsm, spl);
 }
 
 bool config_ok(const sim_config* cfg) {
@@ -535,11 +630,18 @@ int sim_robot_cost(sim_ctx_t* ctx, float* out, int32_t n) {
   if (!out || n < 0 || n > ctx->n) return fail(ctx, SIM_EINVAL, "sim_robot_cost: bad n or NULL out");
   if (n == 0) return SIM_OK;
   CK(cudaSetDevice(ctx->cfg.device));
+  const int n_short = ctx->n - ctx->n_chain;
   std::vector<float> packed(ctx->n);
-  // one float per robot, kScratchFloats apart
-  CK(cudaMemcpy2DAsync(packed.data(), sizeof(float), ctx->d_scratch + b3::kDbgOffset + 31,
-                       b3::kScratchFloats * sizeof(float), sizeof(float), ctx->n, cudaMemcpyDeviceToHost,
-                       ctx->stream));
+  // one float per robot, kScratchFloats (chains: kChainScratchFloats) apart
+  if (n_short > 0)
+    CK(cudaMemcpy2DAsync(packed.data(), sizeof(float), ctx->d_scratch + b3::kDbgOffset + 31,
+                         b3::kScratchFloats * sizeof(float), sizeof(float), n_short, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  if (ctx->n_chain > 0)
+    CK(cudaMemcpy2DAsync(packed.data() + n_short, sizeof(float),
+                         ctx->d_cscratch + b3::kCDbgOffset + b3::kCDbgCycles,
+                         b3::kChainScratchFloats * sizeof(float), sizeof(float), ctx->n_chain,
+                         cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < n; ++i) out[i] = packed[ctx->inv[i]];
   return SIM_OK;
@@ -600,7 +702,9 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
   if (e == cudaSuccess) {
     LaunchArgs args{pop->model_f, pop->model_i, reinterpret_cast<const int4*>(pop->meta), pop->pairs,
                     pop->q,       pop->v,       pop->cpg, pop->status, a.counters, a.scratch, a.lastnc,
-                    nullptr,      nullptr,      pop->n,   make_params(cfg), stream, 0};
+                    nullptr,      nullptr,      pop->n,   make_params(cfg), stream, 0,
+                    0,            nullptr,      nullptr,  nullptr,     nullptr,    nullptr,   nullptr,
+                    nullptr,      nullptr,      nullptr};
     const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
     const int wpsm = cfg->warps_per_sm > 0 ? cfg->warps_per_sm : 16;
     const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : kDefaultStepsPerLaunch;
@@ -678,18 +782,21 @@ int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
   free_population(ctx);
   b3::PackedPopulation pk;
   b3::pack_population(v, n, pk);
-  const std::vector<int>& perm = pk.perm;
-  const std::vector<int>& inv = pk.inv;
-  const std::vector<float>& mf = pk.mf;
-  const std::vector<int>& mi = pk.mi;
-  const std::vector<uint16_t>& pairs = pk.pairs;
-  std::vector<int4> meta(n);
-  for (int k = 0; k < n; ++k) meta[k] = make_int4(pk.meta[4 * k], pk.meta[4 * k + 1], pk.meta[4 * k + 2], pk.meta[4 * k + 3]);
+  const int n_short = n - pk.n_chain;  // warp robots and single free bodies
+  const int n_chain = pk.n_chain;
+  std::vector<int4> meta((size_t)std::max(n_short, 1));
+  for (int k = 0; k < n_short; ++k)
+    meta[k] = make_int4(pk.meta[4 * k], pk.meta[4 * k + 1], pk.meta[4 * k + 2], pk.meta[4 * k + 3]);
+  std::vector<int4> cmeta((size_t)std::max(n_chain, 1));
+  for (int c = 0; c < n_chain; ++c)
+    cmeta[c] = make_int4(pk.cmeta[4 * c], pk.cmeta[4 * c + 1], pk.cmeta[4 * c + 2], pk.cmeta[4 * c + 3]);
   ctx->n = n;
   ctx->n_free = pk.n_free;
-  ctx->perm = perm;
-  ctx->inv = inv;
+  ctx->n_chain = n_chain;
+  ctx->perm = pk.perm;
+  ctx->inv = pk.inv;
   const size_t N = (size_t)n;
+  const size_t NS = (size_t)std::max(n_short, 1), NC = (size_t)std::max(n_chain, 1);
   cudaError_t e;
 #define ALLOC(ptr, bytes)                                         \
   e = cudaMalloc(&(ptr), (bytes));                                \
@@ -697,41 +804,64 @@ int sim_set_population(sim_ctx_t* ctx, const sim_variant_desc* v, int32_t n) {
     free_population(ctx);                                         \
     return fail(ctx, SIM_ENOMEM, std::string("cudaMalloc ") + #ptr); \
   }
-  ALLOC(ctx->d_mf, mf.size() * sizeof(float));
-  ALLOC(ctx->d_mi, mi.size() * sizeof(int));
-  ALLOC(ctx->d_meta, N * sizeof(int4));
-  ALLOC(ctx->d_pairs, pairs.size() * sizeof(uint16_t));
+  ALLOC(ctx->d_mf, std::max(pk.mf.size(), (size_t)1) * sizeof(float));
+  ALLOC(ctx->d_mi, std::max(pk.mi.size(), (size_t)1) * sizeof(int));
+  ALLOC(ctx->d_meta, NS * sizeof(int4));
+  ALLOC(ctx->d_pairs, pk.pairs.size() * sizeof(uint16_t));
   ALLOC(ctx->d_perm, N * sizeof(int));
-  ALLOC(ctx->d_q, N * 32 * sizeof(float));
-  ALLOC(ctx->d_v, N * 32 * sizeof(float));
-  ALLOC(ctx->d_s, N * 64 * sizeof(float));
+  ALLOC(ctx->d_q, NS * 32 * sizeof(float));
+  ALLOC(ctx->d_v, NS * 32 * sizeof(float));
+  ALLOC(ctx->d_s, NS * 64 * sizeof(float));
   ALLOC(ctx->d_fit0, N * 2 * sizeof(float));
   ALLOC(ctx->d_status, N * sizeof(unsigned));
   ALLOC(ctx->d_counters, N * sizeof(Counters));
-  ALLOC(ctx->d_scratch, N * b3::kScratchFloats * sizeof(float));
+  ALLOC(ctx->d_scratch, NS * b3::kScratchFloats * sizeof(float));
   ALLOC(ctx->d_lastnc, N * sizeof(int));
-  ALLOC(ctx->d_order, N * sizeof(int));
+  ALLOC(ctx->d_order, NS * sizeof(int));
   ALLOC(ctx->d_order_hist, 2 * kCostBuckets * sizeof(unsigned));
   ALLOC(ctx->d_stage, N * (SIM_QW + SIM_VW + SIM_SW) * sizeof(float));
   ALLOC(ctx->d_stage_st, N * sizeof(unsigned));
+  ALLOC(ctx->d_cmf, std::max(pk.cmf.size(), (size_t)1) * sizeof(float));
+  ALLOC(ctx->d_cmi, std::max(pk.cmi.size(), (size_t)1) * sizeof(int));
+  ALLOC(ctx->d_cmask, std::max(pk.cmask.size(), (size_t)1) * sizeof(unsigned long long));
+  ALLOC(ctx->d_cmeta, NC * sizeof(int4));
+  ALLOC(ctx->d_cpairs, pk.cpairs.size() * sizeof(uint16_t));
+  ALLOC(ctx->d_cq, NC * SIM_QW * sizeof(float));
+  ALLOC(ctx->d_cv, NC * SIM_VW * sizeof(float));
+  ALLOC(ctx->d_cs, NC * SIM_SW * sizeof(float));
+  ALLOC(ctx->d_cscratch, NC * b3::kChainScratchFloats * sizeof(float));
 #undef ALLOC
-  CK(cudaMemcpyAsync(ctx->d_mf, mf.data(), mf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_mi, mi.data(), mi.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_meta, meta.data(), N * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_pairs, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(ctx->d_mf, pk.mf.data(), pk.mf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_mi, pk.mi.data(), pk.mi.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_meta, meta.data(), NS * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_pairs, pk.pairs.data(), pk.pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_perm, ctx->inv.data(), N * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_q, 0, N * 32 * sizeof(float), ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_v, 0, N * 32 * sizeof(float), ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_s, 0, N * 64 * sizeof(float), ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cmf, pk.cmf.data(), pk.cmf.size() * sizeof(float), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cmi, pk.cmi.data(), pk.cmi.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cmask, pk.cmask.data(), pk.cmask.size() * sizeof(unsigned long long),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cmeta, cmeta.data(), NC * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cpairs, pk.cpairs.data(), pk.cpairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_q, 0, NS * 32 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_v, 0, NS * 32 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_s, 0, NS * 64 * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_cq, 0, NC * SIM_QW * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_cv, 0, NC * SIM_VW * sizeof(float), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_cs, 0, NC * SIM_SW * sizeof(float), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_fit0, 0, N * 2 * sizeof(float), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_status, 0, N * sizeof(unsigned), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_counters, 0, N * sizeof(Counters), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_lastnc, 0, N * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_cscratch, 0, NC * b3::kChainScratchFloats * sizeof(float), ctx->stream));
   // zero scratch, then the size-based cost estimate the first launch is ordered by
-  CK(cudaMemsetAsync(ctx->d_scratch, 0, N * b3::kScratchFloats * sizeof(float), ctx->stream));
-  cost_init<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_meta, n, ctx->d_scratch);
-  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(ctx->d_scratch, 0, NS * b3::kScratchFloats * sizeof(float), ctx->stream));
+  if (n_short > 0) {
+    cost_init<<<(n_short + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_meta, n_short, ctx->d_scratch);
+    CK(cudaGetLastError());
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   return SIM_OK;
 }
@@ -750,8 +880,8 @@ int sim_set_state(sim_ctx_t* ctx, int32_t first, int32_t count, const float* q, 
   CK(cudaMemcpyAsync(sv, v, (size_t)count * SIM_VW * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   if (cpg)
     CK(cudaMemcpyAsync(ss, cpg, (size_t)count * SIM_SW * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-  scatter_state<<<count, 64, 0, ctx->stream>>>(sq, sv, ss, ctx->d_perm, first, count, cpg ? 1 : 0, ctx->d_q,
-                                               ctx->d_v, ctx->d_s, ctx->d_fit0, ctx->d_status);
+  scatter_state<<<count, 128, 0, ctx->stream>>>(sq, sv, ss, ctx->d_perm, first, count, cpg ? 1 : 0, ctx_rows(ctx),
+                                                ctx->d_fit0, ctx->d_status);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
   return SIM_OK;
@@ -794,8 +924,8 @@ int sim_read_state(sim_ctx_t* ctx, int32_t first, int32_t count, float* q, float
   float* dq = ctx->d_stage;
   float* dv = dq + (size_t)count * SIM_QW;
   float* ds = dv + (size_t)count * SIM_VW;
-  gather_state<<<count, 64, 0, ctx->stream>>>(ctx->d_q, ctx->d_v, ctx->d_s, ctx->d_status, ctx->d_perm, first,
-                                              count, dq, dv, ds, ctx->d_stage_st);
+  gather_state<<<count, 128, 0, ctx->stream>>>(ctx_rows(ctx), ctx->d_status, ctx->d_perm, first, count, dq, dv, ds,
+                                               ctx->d_stage_st);
   CK(cudaGetLastError());
   if (q) CK(cudaMemcpyAsync(q, dq, (size_t)count * SIM_QW * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   if (v) CK(cudaMemcpyAsync(v, dv, (size_t)count * SIM_VW * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -815,7 +945,7 @@ int sim_fitness(sim_ctx_t* ctx, float* out, int32_t n) {
   if (n == 0) return SIM_OK;
   CK(cudaSetDevice(ctx->cfg.device));
   float* d_out = ctx->d_stage;
-  fitness_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_q, ctx->d_fit0, ctx->d_perm, n, d_out);
+  fitness_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx_rows(ctx), ctx->d_fit0, ctx->d_perm, n, d_out);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -844,8 +974,8 @@ int sim_set_state_dev(sim_ctx_t* ctx, int32_t first, int32_t count, const float*
   CK(cudaSetDevice(ctx->cfg.device));
   if (!dev_ptr_ok(ctx, q) || !dev_ptr_ok(ctx, v) || !dev_ptr_ok(ctx, cpg))
     return fail(ctx, SIM_EINVAL, "sim_set_state_dev: a buffer is not device memory of the context's device");
-  scatter_state<<<count, 64, 0, ctx->stream>>>(q, v, cpg, ctx->d_perm, first, count, cpg ? 1 : 0, ctx->d_q,
-                                               ctx->d_v, ctx->d_s, ctx->d_fit0, ctx->d_status);
+  scatter_state<<<count, 128, 0, ctx->stream>>>(q, v, cpg, ctx->d_perm, first, count, cpg ? 1 : 0, ctx_rows(ctx),
+                                                ctx->d_fit0, ctx->d_status);
   CK(cudaGetLastError());
   return SIM_OK;
 }
@@ -864,9 +994,8 @@ int sim_read_state_dev(sim_ctx_t* ctx, int32_t first, int32_t count, float* q, f
   float* dq = ctx->d_stage;
   float* dv = dq + (size_t)count * SIM_QW;
   float* ds = dv + (size_t)count * SIM_VW;
-  gather_state<<<count, 64, 0, ctx->stream>>>(ctx->d_q, ctx->d_v, ctx->d_s, ctx->d_status, ctx->d_perm, first,
-                                              count, q ? q : dq, v ? v : dv, cpg ? cpg : ds,
-                                              status ? status : ctx->d_stage_st);
+  gather_state<<<count, 128, 0, ctx->stream>>>(ctx_rows(ctx), ctx->d_status, ctx->d_perm, first, count, q ? q : dq,
+                                               v ? v : dv, cpg ? cpg : ds, status ? status : ctx->d_stage_st);
   CK(cudaGetLastError());
   return SIM_OK;
 }
@@ -879,7 +1008,7 @@ int sim_fitness_dev(sim_ctx_t* ctx, float* out, int32_t n) {
   CK(cudaSetDevice(ctx->cfg.device));
   if (!dev_ptr_ok(ctx, out))
     return fail(ctx, SIM_EINVAL, "sim_fitness_dev: out is not device memory of the context's device");
-  fitness_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_q, ctx->d_fit0, ctx->d_perm, n, out);
+  fitness_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(ctx_rows(ctx), ctx->d_fit0, ctx->d_perm, n, out);
   CK(cudaGetLastError());
   return SIM_OK;
 }
@@ -895,9 +1024,13 @@ int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
   if (ctx->n == 0) return fail(ctx, SIM_ESTATE, "sim_autotune: no population");
   if (probe_steps < 1) return fail(ctx, SIM_EINVAL, "sim_autotune: probe_steps < 1");
   CK(cudaSetDevice(ctx->cfg.device));
+  // the launch shapes are those of the warp-per-robot kernel: long chains
+  // (one block each) sit out the probes and keep their state
+  if (ctx->n == ctx->n_chain) return SIM_OK;
   const size_t N = (size_t)ctx->n;
+  const size_t NS = (size_t)(ctx->n - ctx->n_chain);
   // save state and counters
-  std::vector<float> q(N * 32), v(N * 32), s(N * 64);
+  std::vector<float> q(NS * 32), v(NS * 32), s(NS * 64);
   std::vector<unsigned> st(N);
   std::vector<Counters> cn(N);
   CK(cudaMemcpyAsync(q.data(), ctx->d_q, q.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -932,11 +1065,11 @@ int sim_autotune(sim_ctx_t* ctx, int32_t probe_steps) {
       const bool lk = ctx->lock;
       cudaError_t e = restore();
       if (e != cudaSuccess) break;
-      e = enqueue_steps(ctx, probe_steps, c, lk, occ, probe_steps);  // warm-up (and attribute set-up)
+      e = enqueue_steps(ctx, probe_steps, c, lk, occ, probe_steps, false);  // warm-up (and attribute set-up)
       if (e != cudaSuccess) continue;
       restore();
       cudaEventRecord(e0, ctx->stream);
-      e = enqueue_steps(ctx, probe_steps, c, lk, occ, probe_steps);
+      e = enqueue_steps(ctx, probe_steps, c, lk, occ, probe_steps, false);
       cudaEventRecord(e1, ctx->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess || e != cudaSuccess) continue;
       float ms = 0.f;
@@ -999,8 +1132,10 @@ int sim_debug_contacts(sim_ctx_t* ctx, int32_t i, int32_t max_contacts, float* r
   const int m = std::min(nc, (int)max_contacts);
   std::vector<float> buf((size_t)std::max(m, 1) * b3::kCandW);
   if (m > 0) {
-    CK(cudaMemcpyAsync(buf.data(), ctx->d_scratch + (size_t)d * b3::kScratchFloats, (size_t)m * b3::kCandW * 4,
-                       cudaMemcpyDeviceToHost, ctx->stream));
+    const int n_short = ctx->n - ctx->n_chain;
+    const float* src = d < n_short ? ctx->d_scratch + (size_t)d * b3::kScratchFloats
+                                   : ctx->d_cscratch + (size_t)(d - n_short) * b3::kChainScratchFloats;
+    CK(cudaMemcpyAsync(buf.data(), src, (size_t)m * b3::kCandW * 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   for (int k = 0; k < m; ++k) {
@@ -1023,20 +1158,37 @@ int sim_debug_solver(sim_ctx_t* ctx, int32_t i, float* vfree, float* lambda, int
   if (i < 0 || i >= ctx->n || !vfree || !lambda || !n_out) return fail(ctx, SIM_EINVAL, "sim_debug_solver: bad arguments");
   CK(cudaSetDevice(ctx->cfg.device));
   const int d = ctx->inv[i];
+  const int n_short = ctx->n - ctx->n_chain;
   int nc = 0;
-  std::vector<float> buf(32 + 4 * b3::kCapMax + 16);
   CK(cudaMemcpyAsync(&nc, ctx->d_lastnc + d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(buf.data(), ctx->d_scratch + (size_t)d * b3::kScratchFloats + b3::kDbgOffset,
-                     buf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  for (int k = 0; k < 31; ++k) vfree[k] = buf[k];
-  vfree[31] = 0.f;
-  if (cycles_per_step) {
-    cycles_per_step[0] = buf[31];
-    for (int k = 0; k < b3::kPhases; ++k) cycles_per_step[1 + k] = buf[32 + 4 * b3::kCapMax + k];
+  for (int k = 0; k < SIM_VW; ++k) vfree[k] = 0.f;
+  if (d < n_short) {
+    // warp layout: v_free (32), cycles per step at [31], impulses at 32 + 4k, phases after them
+    std::vector<float> buf(32 + 4 * b3::kCapMax + 16);
+    CK(cudaMemcpyAsync(buf.data(), ctx->d_scratch + (size_t)d * b3::kScratchFloats + b3::kDbgOffset,
+                       buf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 31; ++k) vfree[k] = buf[k];
+    if (cycles_per_step) {
+      cycles_per_step[0] = buf[31];
+      for (int k = 0; k < b3::kPhases; ++k) cycles_per_step[1 + k] = buf[32 + 4 * b3::kCapMax + k];
+    }
+    for (int k = 0; k < nc; ++k)
+      for (int t = 0; t < 3; ++t) lambda[3 * k + t] = buf[32 + 4 * k + t];
+  } else {
+    // chain layout (chain_kernel.cuh)
+    std::vector<float> buf(b3::kCDbgPh + 16);
+    CK(cudaMemcpyAsync(buf.data(), ctx->d_cscratch + (size_t)(d - n_short) * b3::kChainScratchFloats + b3::kCDbgOffset,
+                       buf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < b3::kCV && k < SIM_VW; ++k) vfree[k] = buf[k];
+    if (cycles_per_step) {
+      cycles_per_step[0] = buf[b3::kCDbgCycles];
+      for (int k = 0; k < b3::kPhases; ++k) cycles_per_step[1 + k] = buf[b3::kCDbgPh + k];
+    }
+    for (int k = 0; k < nc; ++k)
+      for (int t = 0; t < 3; ++t) lambda[3 * k + t] = buf[b3::kCDbgLam + 4 * k + t];
   }
-  for (int k = 0; k < nc; ++k)
-    for (int t = 0; t < 3; ++t) lambda[3 * k + t] = buf[32 + 4 * k + t];
   *n_out = nc;
   return SIM_OK;
 }

@@ -39,6 +39,11 @@ enum : int {
 };
 // per-variant int model fields, [field][32 body slots]
 enum : int { I_PARENT = 0, I_AXIS, I_PATH, I_CHILD, I_DEPTH, NI = 5 };
+// chain layout (robots of more than kMaxB bodies, up to 64): the float fields
+// above over 64 body slots, int fields [CNI][64] and 64-bit masks [CNM][64]
+constexpr int kChainSlots = 64;
+enum : int { CI_PARENT = 0, CI_AXIS, CI_DEPTH, CNI = 3 };
+enum : int { CM_PATH = 0, CM_CHILD, CNM = 2 };
 
 struct StepParams {
   float dt, gx, gy, gz;
@@ -122,7 +127,8 @@ __host__ __device__ __forceinline__ void quat_to_R(float qw, float qx, float qy,
   R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
 }
 
-__host__ __device__ __forceinline__ void axis_of(const float (*R)[32], int b, int k, float* o) {
+template <int NS = 32>
+__host__ __device__ __forceinline__ void axis_of(const float (*R)[NS], int b, int k, float* o) {
   o[0] = R[k][b]; o[1] = R[3 + k][b]; o[2] = R[6 + k][b];
 }
 
@@ -142,15 +148,17 @@ __host__ __device__ __forceinline__ void put_candidate(float* cand, int n, const
 // (8 floats each, candidate layout); returns their count.  Axis choice:
 // minimum overlap, ties to the lowest index, a face unless the best edge
 // overlap is below 0.95 x the best face overlap.  Normals point from b to a.
-__host__ __device__ __noinline__ int box_box_lane(const float (*RR)[32], const float (*CC)[32],
+// NS: body slots per field of RR, CC and the model F (32, or 64 for chains).
+template <int NS = 32>
+__host__ __device__ __noinline__ int box_box_lane(const float (*RR)[NS], const float (*CC)[NS],
                                                   const float* __restrict__ F, int a, int b, float* out) {
   float Ax[3][3], Bx[3][3], hA[3], hB[3], D[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    axis_of(RR, a, k, Ax[k]);
-    axis_of(RR, b, k, Bx[k]);
-    hA[k] = F[(F_HALF + k) * 32 + a];
-    hB[k] = F[(F_HALF + k) * 32 + b];
+    axis_of<NS>(RR, a, k, Ax[k]);
+    axis_of<NS>(RR, b, k, Bx[k]);
+    hA[k] = F[(F_HALF + k) * NS + a];
+    hB[k] = F[(F_HALF + k) * NS + b];
     D[k] = CC[k][b] - CC[k][a];
   }
   float fbest = 0.f, ebest = 0.f, min_ov = 0.f;
@@ -333,12 +341,13 @@ __host__ __device__ __noinline__ int box_box_lane(const float (*RR)[32], const f
 // sphere centre C clamped to the box in box axes; C outside the box: normal
 // along C - Q, depth r - |C - Q|; C inside: the nearest face's normal
 // (smallest h_k - |C_k|, ties to the lowest k), depth r + h_k - |C_k|.
-__host__ __device__ __noinline__ int sphere_pair_lane(const float (*RR)[32], const float (*CC)[32],
+template <int NS = 32>
+__host__ __device__ __noinline__ int sphere_pair_lane(const float (*RR)[NS], const float (*CC)[NS],
                                                       const float* __restrict__ F, int a, int b, float* out) {
-  const bool sa = F[F_GEOM * 32 + a] != 0.f, sb = F[F_GEOM * 32 + b] != 0.f;
+  const bool sa = F[F_GEOM * NS + a] != 0.f, sb = F[F_GEOM * NS + b] != 0.f;
   float n[3], p[3], depth;
   if (sa && sb) {
-    const float ra = F[F_HALF * 32 + a], rb = F[F_HALF * 32 + b];
+    const float ra = F[F_HALF * NS + a], rb = F[F_HALF * NS + b];
     const float d[3] = {CC[0][a] - CC[0][b], CC[1][a] - CC[1][b], CC[2][a] - CC[2][b]};
     const float dist = sqrtf(dot3(d, d));
     depth = ra + rb - dist;
@@ -349,15 +358,15 @@ __host__ __device__ __noinline__ int sphere_pair_lane(const float (*RR)[32], con
     }
   } else {
     const int is = sa ? a : b, ix = sa ? b : a;  // the sphere and the box
-    const float r = F[F_HALF * 32 + is];
+    const float r = F[F_HALF * NS + is];
     float h[3], D[3], l[3], q[3], e[3];
     for (int k = 0; k < 3; ++k) {
-      h[k] = F[(F_HALF + k) * 32 + ix];
+      h[k] = F[(F_HALF + k) * NS + ix];
       D[k] = CC[k][is] - CC[k][ix];
     }
     for (int k = 0; k < 3; ++k) {
       float ax[3];
-      axis_of(RR, ix, k, ax);
+      axis_of<NS>(RR, ix, k, ax);
       l[k] = dot3(ax, D);
       q[k] = fminf(fmaxf(l[k], -h[k]), h[k]);
       e[k] = l[k] - q[k];
@@ -396,10 +405,11 @@ __host__ __device__ __noinline__ int sphere_pair_lane(const float (*RR)[32], con
 // Narrow phase of one body pair a < b on one lane, by geometry: box/box, or
 // sphere/box and sphere/sphere.  Rows to `out` (candidate layout); returns
 // their count.
-__host__ __device__ __noinline__ int body_pair_lane(const float (*RR)[32], const float (*CC)[32],
+template <int NS = 32>
+__host__ __device__ __noinline__ int body_pair_lane(const float (*RR)[NS], const float (*CC)[NS],
                                                     const float* __restrict__ F, int a, int b, float* out) {
-  if (F[F_GEOM * 32 + a] != 0.f || F[F_GEOM * 32 + b] != 0.f) return sphere_pair_lane(RR, CC, F, a, b, out);
-  return box_box_lane(RR, CC, F, a, b, out);
+  if (F[F_GEOM * NS + a] != 0.f || F[F_GEOM * NS + b] != 0.f) return sphere_pair_lane<NS>(RR, CC, F, a, b, out);
+  return box_box_lane<NS>(RR, CC, F, a, b, out);
 }
 
 // Double-precision sine and cosine of one argument, compact enough to live in

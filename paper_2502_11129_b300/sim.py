@@ -17,8 +17,9 @@ from . import population as popmod
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libb3sim.so")
 
-SIM_MAX_BODIES = 26
-SIM_QW, SIM_VW, SIM_SW = 32, 32, 64
+SIM_MAX_BODIES = 64
+SIM_WARP_MAX_BODIES = 26
+SIM_QW, SIM_VW, SIM_SW = 72, 72, 128
 SIM_MAX_CONTACT_CAP = 64
 ST_NONFINITE, ST_OVERFLOW, ST_CHOL, ST_CANDIDATES = 1, 2, 4, 8
 STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ECUDA", -3: "SIM_ENOMEM", -4: "SIM_ESTATE"}
@@ -45,7 +46,7 @@ class SimConfig(C.Structure):
 class VariantDesc(C.Structure):
     _fields_ = [
         ("n_bodies", C.c_int32), ("parent", C.POINTER(C.c_int8)), ("hinge_axis", C.POINTER(C.c_int8)),
-        ("exclude", C.POINTER(C.c_uint32)), ("joint_frame", C.POINTER(C.c_float)),
+        ("exclude", C.POINTER(C.c_uint64)), ("joint_frame", C.POINTER(C.c_float)),
         ("half_size", C.POINTER(C.c_float)), ("box_center", C.POINTER(C.c_float)),
         ("mass", C.POINTER(C.c_float)), ("cpg_w_internal", C.POINTER(C.c_float)),
         ("cpg_w_couple", C.POINTER(C.c_float)), ("geom", C.POINTER(C.c_int8)),
@@ -124,7 +125,7 @@ class Population32:
         self.n = n
         self.parent = np.ascontiguousarray(pop.parent, dtype=np.int8)
         self.axis = np.ascontiguousarray(pop.axis, dtype=np.int8)
-        self.exclude = np.ascontiguousarray(pop.exclude, dtype=np.uint32)
+        self.exclude = np.ascontiguousarray(pop.exclude, dtype=np.uint64)
         jf = np.concatenate([pop.R_fix, pop.p_fix], axis=2)
         self.joint_frame = np.ascontiguousarray(jf, dtype=np.float32)
         self.half = np.ascontiguousarray(pop.half, dtype=np.float32)
@@ -140,7 +141,7 @@ class Population32:
             d.n_bodies = int(pop.nb[i])
             d.parent = self.parent[i].ctypes.data_as(C.POINTER(C.c_int8))
             d.hinge_axis = self.axis[i].ctypes.data_as(C.POINTER(C.c_int8))
-            d.exclude = self.exclude[i].ctypes.data_as(C.POINTER(C.c_uint32))
+            d.exclude = self.exclude[i].ctypes.data_as(C.POINTER(C.c_uint64))
             d.joint_frame = self.joint_frame[i].ctypes.data_as(f)
             d.half_size = self.half[i].ctypes.data_as(f)
             d.box_center = self.com[i].ctypes.data_as(f)

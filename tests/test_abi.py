@@ -90,3 +90,16 @@ def test_step_kernel_fp64_sincos_against_libm():
         assert np.abs(s - np.sin(x)).max() <= tol
         assert np.abs(c - np.cos(x)).max() <= tol
     assert S.lib().sim_debug_sincos(None, 1, None, None) == -1  # SIM_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """Row strides and body bounds of the binding are those of include/b3sim.h."""
+    text = open(os.path.join(ROOT, "include", "b3sim.h")).read()
+    val = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(SIM_[A-Z_]+)\s+(\d+)", text)}
+    assert val["SIM_MAX_BODIES"] == S.SIM_MAX_BODIES == 64
+    assert val["SIM_WARP_MAX_BODIES"] == S.SIM_WARP_MAX_BODIES
+    assert (val["SIM_QW"], val["SIM_VW"], val["SIM_SW"]) == (S.SIM_QW, S.SIM_VW, S.SIM_SW)
+    # rows hold the largest robot: nq = nb + 6, nv = nb + 5, 2 (nb - 1) CPG states
+    assert S.SIM_QW >= S.SIM_MAX_BODIES + 6 and S.SIM_VW >= S.SIM_MAX_BODIES + 5
+    assert S.SIM_SW >= 2 * (S.SIM_MAX_BODIES - 1)
+    assert val["SIM_MAX_CONTACT_CAP"] == S.SIM_MAX_CONTACT_CAP

@@ -275,10 +275,10 @@ def test_launch_shapes_and_phase_lock_agree_bitwise():
 
 
 def test_one_step_largest_robots_26_bodies():
-    """The maximum model size (25 hinges: 26 bodies, 31 dofs, every lane of
-    the warp a dof) in random poses against the oracle."""
+    """The largest robots of the warp-per-robot kernel (25 hinges: 26 bodies,
+    31 dofs, every lane of the warp a dof) in random poses against the oracle."""
     pop = P.grammar(48, seed=51, hinges=(25, 25))
-    assert (pop.nb == S.SIM_MAX_BODIES).all()
+    assert (pop.nb == S.SIM_WARP_MAX_BODIES).all()
     q, v, s = P.random_state(pop, seed=52)
     q[:, 2] = pop.q0[:, 2] + np.random.default_rng(53).uniform(-0.03, 0.0, pop.n)
     r, y, gst, _ = _one_step(pop, q, v, s)

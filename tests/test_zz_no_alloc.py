@@ -109,8 +109,10 @@ def _device_pop(pop, Q, V, Sx):
     import torch
     dev = torch.device("cuda", 0)
     mf, mi, meta, pairs = pack(pop)
+    # the device rows of this layout are 32, 32 and 64 floats wide (the host rows are wider)
     t = {k: torch.from_numpy(np.ascontiguousarray(a)).to(dev) for k, a in
-         dict(mf=mf, mi=mi, meta=meta, pairs=pairs.view(np.int16), q=Q, v=V, s=Sx).items()}
+         dict(mf=mf, mi=mi, meta=meta, pairs=pairs.view(np.int16), q=Q[:, :32], v=V[:, :32],
+              s=Sx[:, :64]).items()}
     t["st"] = torch.zeros(pop.n, dtype=torch.int32, device=dev)
     dp = S.DevicePopulation(pop.n, t["mf"].data_ptr(), t["mi"].data_ptr(), t["meta"].data_ptr(),
                             t["pairs"].data_ptr(), t["q"].data_ptr(), t["v"].data_ptr(), t["s"].data_ptr(),
@@ -140,6 +142,7 @@ def test_noalloc_matches_context_entry_on_two_calls():
         torch.cuda.synchronize(dev)
         ref.step(60)
         rq, rv, rs, rst = ref.read_state()
+        rq, rv, rs = rq[:, :32], rv[:, :32], rs[:, :64]
         gq, gv, gs = t["q"].cpu().numpy(), t["v"].cpu().numpy(), t["s"].cpu().numpy()
         gst = t["st"].cpu().numpy().view(np.uint32)
         assert np.array_equal(gst, rst), call
