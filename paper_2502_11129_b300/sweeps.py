@@ -11,11 +11,13 @@ simulator:
 
 Scenes: ``box`` (one free 0.1 m cube per variant, the BOX-like scene),
 ``box_and_ball`` (a cube with one hinged ball, the BOX_AND_BALL-like scene),
-``rope`` (a cube trailing a passive 25-link chain, the ARM_WITH_ROPE-like
-scene), ``quadruped``, ``grammar`` (tree-grammar robots with 2..20 hinges)
-and ``grammar_balls`` (the same with 30 % of the modules balls).  Large
-populations other than ``box`` repeat a base population of 4096 distinct
-robots (generating robots is host work that the sweep does not time).
+``rope`` (a cube trailing a passive chain, 25 links by default: the
+ARM_WITH_ROPE-like scene; ``--links`` up to 63, where chains of more than 25
+links take the block-per-robot kernel), ``quadruped``, ``grammar``
+(tree-grammar robots with 2..20 hinges) and ``grammar_balls`` (the same with
+30 % of the modules balls).  Large populations other than ``box`` repeat a
+base population of 4096 distinct robots (generating robots is host work that
+the sweep does not time).
 
 Each point: build the population and the simulator, one untimed call that
 captures the CUDA graph for that step count, then 3 timed calls, each from
@@ -50,22 +52,25 @@ _MAKERS = {
     "grammar": lambda n, seed: P.grammar(n, seed=seed),
     "grammar_balls": lambda n, seed: P.grammar(n, seed=seed, ball_p=0.3),
     "box_and_ball": lambda n, seed: P.box_and_ball(n, seed=seed),
-    "rope": lambda n, seed: P.rope(n, seed=seed),
+    "rope": lambda n, seed, links=25: P.rope(n, seed=seed, links=links),
 }
 SCENES = ("box",) + tuple(_MAKERS)
 # simulator settings a scene runs with (a rope is a passive chain)
 SCENE_CFG = {"rope": dict(actuate=0)}
 
 
-def scene(name: str, n: int, seed: int = 1) -> P.Population:
+def scene(name: str, n: int, seed: int = 1, links: int | None = None) -> P.Population:
     if name == "box":
         return P.boxes(n, seed=seed)
     if name not in _MAKERS:
         raise ValueError(f"unknown scene {name!r}")
+    if links is not None and name != "rope":
+        raise ValueError("links applies to the rope scene only")
     base_n = min(n, BASE_ROBOTS)
-    key = (name, seed)
+    key = (name, seed, links)
     if key not in _BASE or _BASE[key].n < base_n:
-        _BASE[key] = _MAKERS[name](base_n, seed)
+        extra = {} if links is None else {"links": links}
+        _BASE[key] = _MAKERS[name](base_n, seed, **extra)
     base = _BASE[key]
     return base.subset(np.arange(n) % base.n)
 
@@ -96,19 +101,21 @@ def time_point(pop: P.Population, steps: int, reps: int = 3, **cfg) -> dict:
                 contacts_per_variant_step=c["contacts"] / max(c["variant_steps"], 1))
 
 
-def sweep(kind: str, scene_name: str, values=None, reps: int = 3, seed: int = 1, log=print) -> list:
+def sweep(kind: str, scene_name: str, values=None, reps: int = 3, seed: int = 1, log=print,
+          links: int | None = None) -> list:
     rows = []
+    label = scene_name if links is None else f"{scene_name}-{links}"
     if kind == "variants":
         for n in values or PAPER_VARIANTS:
-            r = time_point(scene(scene_name, n, seed), 1000, reps, **SCENE_CFG.get(scene_name, {}))
-            r["scene"] = scene_name
+            r = time_point(scene(scene_name, n, seed, links), 1000, reps, **SCENE_CFG.get(scene_name, {}))
+            r["scene"] = label
             rows.append(r)
             log(json.dumps(r))
     elif kind == "steps":
-        pop = scene(scene_name, 128, seed)
+        pop = scene(scene_name, 128, seed, links)
         for s in values or PAPER_STEPS:
             r = time_point(pop, s, reps, **SCENE_CFG.get(scene_name, {}))
-            r["scene"] = scene_name
+            r["scene"] = label
             rows.append(r)
             log(json.dumps(r))
     else:
@@ -131,8 +138,9 @@ def main():
     ap.add_argument("--values", type=int, nargs="*")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--links", type=int, default=None, help="chain length of the rope scene (1..63)")
     a = ap.parse_args()
-    rows = sweep(a.sweep, a.scene, a.values, a.reps, a.seed)
+    rows = sweep(a.sweep, a.scene, a.values, a.reps, a.seed, links=a.links)
     print(table(rows))
 
 

@@ -20,6 +20,10 @@ def test_scene_sizes_and_tiling(monkeypatch):
     assert np.all(bb.nb == 2) and np.all(bb.geom[:, 1] == 1) and np.all(bb.geom[:, 0] == 0)
     r = SW.scene("rope", 3)
     assert np.all(r.nb == 26) and SW.SCENE_CFG["rope"] == dict(actuate=0)
+    r63 = SW.scene("rope", 3, links=63)
+    assert np.all(r63.nb == 64) and r63.slots == 64
+    with pytest.raises(ValueError):
+        SW.scene("grammar", 3, links=40)
     gb = SW.scene("grammar_balls", 40)
     assert (gb.geom == 1).any()
     # a ball is always a leaf
