@@ -136,6 +136,7 @@ __device__ __forceinline__ void warp_sum3(float& a, float& b, float& c, int lane
 // forward substitution of L y = b with lane = dof; returns y on each lane
 __device__ __forceinline__ float lower_solve(const WarpSmem& sm, float b, int nv, int lane) {
   float acc = b, y = 0.f;
+#pragma unroll 1
   for (int i = 0; i < nv; ++i) {
     float yi = shf(acc, i) * sm.invd[i];
     if (lane == i) y = yi;
@@ -147,12 +148,132 @@ __device__ __forceinline__ float lower_solve(const WarpSmem& sm, float b, int nv
 // back substitution of L^T x = y with lane = dof
 __device__ __forceinline__ float upper_solve(const WarpSmem& sm, float y, int nv, int lane) {
   float acc = y, x = 0.f;
+#pragma unroll 1
   for (int i = nv - 1; i >= 0; --i) {
     float xi = shf(acc, i) * sm.invd[i];
     if (lane == i) x = xi;
     if (lane < i) acc -= sm.M[tri(i) + lane] * xi;
   }
   return x;
+}
+
+// Keep the cap deepest of ncand candidates (ties by list order), list order
+// kept: ranks of every candidate first, then an in-order compaction
+// (destination <= source).  Out of line: it runs only on steps whose
+// candidates overflow the cap, and its code stays out of the step loop.
+static_assert(kCandW == 8, "a candidate row moves as two float4");
+static __device__ __noinline__ void keep_deepest(float* cand, int ncand, int cap, unsigned* keep_bits, int lane) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < ncand; i0 += 32) {
+    const int i = i0 + lane;
+    bool keep = false;
+    if (i < ncand) {
+      const float di = cand[(size_t)i * kCandW + 6];
+      int rank = 0;
+#pragma unroll 1
+      for (int j = 0; j < ncand; ++j) {
+        const float dj = cand[(size_t)j * kCandW + 6];
+        rank += (dj > di || (dj == di && j < i)) ? 1 : 0;
+      }
+      keep = rank < cap;
+    }
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (lane == 0) keep_bits[i0 >> 5] = bal;
+  }
+  __syncwarp();
+  int kept = 0;
+#pragma unroll 1
+  for (int i0 = 0; i0 < ncand; i0 += 32) {
+    const int i = i0 + lane;
+    const unsigned bal = keep_bits[i0 >> 5];
+    const bool keep = (bal >> lane) & 1u;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    if (keep) {
+      const float4* src = reinterpret_cast<const float4*>(cand + (size_t)i * kCandW);
+      r0 = src[0];
+      r1 = src[1];
+    }
+    __syncwarp();
+    if (keep) {
+      float4* dst = reinterpret_cast<float4*>(cand + (size_t)(kept + __popc(bal & ((1u << lane) - 1u))) * kCandW);
+      dst[0] = r0;
+      dst[1] = r1;
+    }
+    kept += __popc(bal);
+    __syncwarp();
+  }
+}
+
+// Gauss-Seidel sweeps of more than 10 contacts in dof space; returns u (this
+// lane's dof) and leaves every contact's impulses in lamS.  Out of line, so
+// that its code sits outside the step loop that most robots run.
+static __device__ __noinline__ float dof_space_sweep(float4* lamS, const float* __restrict__ cstg,
+                                                     const float* __restrict__ Yg, int nc, int iters, float mu,
+                                                     int lane) {
+  // Dof space (lane = dof, u = L^T (v - v_free)), one contact of
+  // lookahead: the next contact's row products are reduced over the warp
+  // from u before the current update lands, then brought up to date with
+  // B_k (u changes by Y_k^T dlam_k), so that the five-level reduction
+  // runs beside the update instead of ahead of it.  Contact impulses sit
+  // in shared memory: every lane computes and stores them alike and reads
+  // back its own writes.
+#pragma unroll 1
+  for (int k0 = lane; k0 < nc; k0 += 32) lamS[k0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
+  const float4* c4 = reinterpret_cast<const float4*>(cstg);
+  // more than 10 contacts here: the next contact is never the current one
+  int k = 0, kn = 1;
+  float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
+  const float* Zn = Yg + (size_t)(3 * kn) * 32;
+  float z0 = Zn[lane], z1 = Zn[32 + lane], z2 = Zn[64 + lane];
+  float u = 0.f;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // Y_k . u before update k (u = 0 at the start)
+  float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of contact k
+  const int nupd = iters * nc;
+#pragma unroll 1
+  for (int upd = 0; upd < nupd; ++upd) {
+    const int knn = (kn + 1 < nc) ? kn + 1 : 0;
+    // this contact's constants and coupling block B_k (loaded first, used
+    // after the reduction's shuffles); the next one's impulses and the
+    // rows after it
+    const float4 ca = c4[6 * k], cb4 = c4[6 * k + 1], cc4 = c4[6 * k + 2];
+    const float4 bq0 = c4[6 * k + 3], bq1 = c4[6 * k + 4], bq2 = c4[6 * k + 5];
+    const float4 nl = lamS[kn];
+    const float* Zz = Yg + (size_t)(3 * knn) * 32;
+    const float zz0 = Zz[lane], zz1 = Zz[32 + lane], zz2 = Zz[64 + lane];
+    // the next contact's row products against u before this update
+    float p0 = z0 * u, p1 = z1 * u, p2 = z2 * u;
+    warp_sum3(p0, p1, p2, lane);
+    // constants: (b_n, inv_n, R_n, b_t1), (inv_t1, R_t1, b_t2, inv_t2), (R_t2, A_t1n, A_t2n, 0)
+    const float gn = s0 + ca.x + ca.z * ln;
+    const float lnn = fmaxf(0.f, ln - gn * ca.y);
+    const float dn = lnn - ln;
+    const float g1 = s1 + cc4.y * dn + ca.w + cb4.y * l1;
+    const float g2 = s2 + cc4.z * dn + cb4.z + cc4.x * l2;
+    float l1t = l1 - g1 * cb4.x;
+    float l2t = l2 - g2 * cb4.w;
+    const float lim = mu * lnn;
+    const float nt2 = l1t * l1t + l2t * l2t;
+    const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+    l1t *= sc;
+    l2t *= sc;
+    const float d1 = l1t - l1, d2 = l2t - l2;
+    u += y0 * dn + y1 * d1 + y2 * d2;
+    lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
+    // B_k row-major in bq0..bq2: (b00 b01 b02 b10) (b11 b12 b20 b21) (b22 ...)
+    s0 = p0 + bq0.x * dn + bq0.y * d1 + bq0.z * d2;
+    s1 = p1 + bq0.w * dn + bq1.x * d1 + bq1.y * d2;
+    s2 = p2 + bq1.z * dn + bq1.w * d1 + bq2.x * d2;
+    ln = nl.x;
+    l1 = nl.y;
+    l2 = nl.z;
+    y0 = z0; y1 = z1; y2 = z2;
+    z0 = zz0; z1 = zz1; z2 = zz2;
+    k = kn;
+    kn = knn;
+  }
+  __syncwarp();
+  return u;
 }
 
 struct Counters {
@@ -274,6 +395,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       float dx = wint * yo, dy = -wint * xo;
       const float xp = shf(xo, par0);
       if (hinge && parent >= 1) dx -= wcpl * xp;
+#pragma unroll 1
       for (unsigned m = hinge ? childm : 0u; m; m &= m - 1) dx += sm.acc[0][__ffs(m) - 1];
       __syncwarp();
       xn = xo + dt * dx;
@@ -309,6 +431,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       const float pf0 = fld(F_PFIX), pf1 = fld(F_PFIX + 1), pf2 = fld(F_PFIX + 2);
 #pragma unroll
       for (int k2 = 0; k2 < 9; ++k2) R[k2] = R0[k2];
+#pragma unroll 1
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
         float Rp[9], rp[3];
 #pragma unroll
@@ -347,6 +470,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int t = 0; t < 9; ++t) Fr[t] = fld(F_RFIX + t);
 #pragma unroll
       for (int t = 0; t < 3; ++t) Fp[t] = fld(F_PFIX + t);
+#pragma unroll 1
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
         const f2 p0 = f2_shf(hz0, par0), p1 = f2_shf(hz1, par0), p2 = f2_shf(hz2, par0), pb = f2_shf(hzb, par0);
         if (depth == lvl) {
@@ -429,6 +553,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         ab[0] = 0.f; ab[1] = 0.f; ab[2] = 0.f;
         ab[3] = vxw[0] - P.gx; ab[4] = vxw[1] - P.gy; ab[5] = vxw[2] - P.gz;
       }
+#pragma unroll 1
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
         float vp[6], ap[6];
 #pragma unroll
@@ -454,6 +579,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     __syncwarp();
     // leaf-to-root sums of forces and inertias, lane = component
     if (lane < 16) {
+#pragma unroll 1
       for (int b = nb - 1; b >= 1; --b) {
         const int p = sm.parent[b];
         sm.acc[lane][p] += sm.acc[lane][b];
@@ -477,6 +603,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 
     // ---------------- 4. CRBA mass matrix (packed lower triangle)
     if (lane < nv)
+#pragma unroll 1
       for (int j = 0; j <= lane; ++j) sm.M[tri(lane) + j] = 0.f;
     __syncwarp();
     if (hinge) {
@@ -488,6 +615,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       const int ti = tri(i);
       sm.M[ti + i] = Sb[0] * Fv[0] + Sb[1] * Fv[1] + Sb[2] * Fv[2] + Sb[3] * Fv[3] + Sb[4] * Fv[4] + Sb[5] * Fv[5] +
                      P.armature;
+#pragma unroll 1
       for (int j = parent; j > 0; j = sm.parent[j]) {
         const int jj = 5 + j;
         sm.M[ti + jj] = sm.S[0][jj] * Fv[0] + sm.S[1][jj] * Fv[1] + sm.S[2][jj] * Fv[2] + sm.S[3][jj] * Fv[3] +
@@ -505,6 +633,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 #pragma unroll
       for (int k = 0; k < 6; ++k) Sk[k] = sm.S[k][lane];
       inertia_apply(Ic, Sk, Fv);
+#pragma unroll 1
       for (int l = lane; l < 6; ++l)
         sm.M[tri(l) + lane] = sm.S[0][l] * Fv[0] + sm.S[1][l] * Fv[1] + sm.S[2][l] * Fv[2] + sm.S[3][l] * Fv[3] +
                               sm.S[4][l] * Fv[4] + sm.S[5][l] * Fv[5];
@@ -522,6 +651,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     {
       const float* Li = sm.M + tri(lane);
       const bool row = lane < nv;
+#pragma unroll 1
       for (int j = 0; j < nv; ++j) {
         const float* Lj = sm.M + tri(j);
         float s0 = 0.f, s1 = 0.f;
@@ -592,6 +722,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       int off = incl - cnt;
       const float up[3] = {0.f, 0.f, 1.f};
+#pragma unroll 1
       for (unsigned mm = mask8; mm; mm &= mm - 1) {
         const int k = __ffs(mm) - 1;
         const float l0 = c0 + ((k & 1) ? h0 : -h0), l1 = c1 + ((k & 2) ? h1 : -h1), l2 = c2 + ((k & 4) ? h2 : -h2);
@@ -616,6 +747,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       // into shared memory, so that the narrow phase below runs once per 32
       // near pairs rather than once per 32 candidate pairs
       int nnear = 0;
+#pragma unroll 1
       for (int p0 = 0; p0 < npairs; p0 += 32) {
         const int pi = p0 + lane;
         bool near = false;
@@ -636,6 +768,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       __syncwarp();
       // narrow phase, lane = near pair; contacts placed in pair order by a warp scan
       float* stage = cand + kStageOffset + (size_t)lane * 8 * kCandW;
+#pragma unroll 1
       for (int q0 = 0; q0 < nnear; q0 += 32) {
         const int qi = q0 + lane;
         int cnt = 0;
@@ -650,6 +783,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           if (lane >= o) incl += t;
         }
         const int off = ncand + incl - cnt;
+#pragma unroll 1
         for (int i = 0; i < cnt; ++i) {
           if (off + i < kCand) {
 #pragma unroll
@@ -668,41 +802,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     int nc = ncand;
     if (ncand > P.cap) {
       st |= 2u;
-      for (int i0 = 0; i0 < ncand; i0 += 32) {
-        const int i = i0 + lane;
-        bool keep = false;
-        if (i < ncand) {
-          const float di = cand[(size_t)i * kCandW + 6];
-          int rank = 0;
-          for (int j = 0; j < ncand; ++j) {
-            const float dj = cand[(size_t)j * kCandW + 6];
-            rank += (dj > di || (dj == di && j < i)) ? 1 : 0;
-          }
-          keep = rank < P.cap;
-        }
-        const unsigned bal = __ballot_sync(kFull, keep);
-        if (lane == 0) sm.keep[i0 >> 5] = bal;
-      }
-      __syncwarp();
-      int kept = 0;
-      for (int i0 = 0; i0 < ncand; i0 += 32) {
-        const int i = i0 + lane;
-        const unsigned bal = sm.keep[i0 >> 5];
-        const bool keep = (bal >> lane) & 1u;
-        float row[kCandW];
-        if (keep) {
-#pragma unroll
-          for (int k = 0; k < kCandW; ++k) row[k] = cand[(size_t)i * kCandW + k];
-        }
-        __syncwarp();
-        if (keep) {
-          const int dst = kept + __popc(bal & ((1u << lane) - 1u));
-#pragma unroll
-          for (int k = 0; k < kCandW; ++k) cand[(size_t)dst * kCandW + k] = row[k];
-        }
-        kept += __popc(bal);
-        __syncwarp();
-      }
+      keep_deepest(cand, ncand, P.cap, sm.keep, lane);
       nc = P.cap;
     }
     n_contacts += (unsigned)nc;
@@ -713,6 +813,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     B3_LOCK();
     // ---------------- 7. contact rows: Y_r = L^-1 J_r^T and Gauss-Seidel constants (lane = row)
     float w_row = 0.f;  // with at most 32 rows: this lane's row residual J_r v_free - bias
+#pragma unroll 1
     for (int r0 = 0; r0 < 3 * nc; r0 += 32) {
       const int row = r0 + lane;
       const bool act = row < 3 * nc;
@@ -756,6 +857,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         jv += Jj * sm.vfree[j];
         yr[32 * j] = Jj;
       }
+#pragma unroll 1
       for (int j = nv; j < 32; ++j) yr[32 * j] = 0.f;
       // forward substitution y <- L^-1 y, L broadcast from shared memory
       float aa = 0.f;
@@ -798,6 +900,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     // contact), and for the dof-space sweep (more than 10 contacts) the block
     // B_k = Y_(k+1) Y_k^T to the next contact in sweep order
     const bool dofspace = 3 * nc > 32;
+#pragma unroll 1
     for (int k0 = 0; k0 < nc; k0 += 32) {
       const int k = k0 + lane;
       if (k < nc) {
@@ -884,52 +987,61 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         __syncwarp();
       }
       // Staging in the rotation rows of shared memory (free during the
-      // sweep): the Gauss-Seidel constants of every contact and the
-      // impulses of every contact, which all lanes compute alike and store
-      // alike, so each lane later reads back its own write.
+      // sweep): the Gauss-Seidel constants of every contact, two float4
+      // (1/(A+R)_n, R_n, 1/(A+R)_t1, R_t1), (1/(A+R)_t2, R_t2, A_t1n, A_t2n),
+      // and the impulses of every contact, which all lanes compute alike and
+      // store alike, so each lane later reads back its own write.
       float4* lamS = reinterpret_cast<float4*>(&sm.R[0][0]);
       float4* cS = lamS + 12;
-      {
-        const float4* c4 = reinterpret_cast<const float4*>(cstg);
-        if (lane < 3 * nc) cS[lane] = c4[2 * lane - lane % 3];  // 3 of the 6 float4 of each contact
-        if (lane < nc) lamS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lane < nc) {
+        const float4* c4 = reinterpret_cast<const float4*>(cstg) + 6 * lane;
+        const float4 x0 = c4[0], x1 = c4[1], x2 = c4[2];
+        cS[2 * lane] = make_float4(x0.y, x0.z, x1.x, x1.y);
+        cS[2 * lane + 1] = make_float4(x1.w, x2.x, x2.y, x2.z);
+        lamS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
       float w = w_row;
-      float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of the contact being updated
-      const int nupd = P.iters * nc;
-      int k = 0;
-      for (int upd = 0; upd < nupd; ++upd) {
-        const int kn = (k + 1 < nc) ? k + 1 : 0;
-        const int r = 3 * k;
-        // this contact's constants and this lane's row of A in its columns
-        // (loaded first, used after the shuffles), the next one's impulses
-        const float4 ca = cS[r], cb4 = cS[r + 1], cc4 = cS[r + 2];
-        const float an = sm.Yt[r][lane], a1 = sm.Yt[r + 1][lane], a2 = sm.Yt[r + 2][lane];
-        const float4 nl = lamS[kn];  // stale only when kn == k
-        const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
-        const float gn = wn + ca.z * ln;
-        const float lnn = fmaxf(0.f, ln - gn * ca.y);
-        const float dn = lnn - ln;
-        const float g1 = w1 + cc4.y * dn + cb4.y * l1;
-        const float g2 = w2 + cc4.z * dn + cc4.x * l2;
-        float l1t = l1 - g1 * cb4.x;
-        float l2t = l2 - g2 * cb4.w;
-        const float lim = P.mu * lnn;
-        const float nt2 = l1t * l1t + l2t * l2t;
-        const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
-        l1t *= sc;
-        l2t *= sc;
-        w += an * dn + a1 * (l1t - l1) + a2 * (l2t - l2);
-        lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
-        const bool same = kn == k;
-        ln = same ? lnn : nl.x;
-        l1 = same ? l1t : nl.y;
-        l2 = same ? l2t : nl.z;
-        k = kn;
+      // sweeps over contacts 0 .. nc - 1 in order; the impulses of the next
+      // contact are read one update ahead (lamS[nc] is spare: at the last
+      // contact of a sweep the read is discarded, and the next sweep starts
+      // from contact 0's, written back by its update)
+#pragma unroll 1
+      for (int it = 0; it < P.iters; ++it) {
+        const float4 l0 = lamS[0];
+        float ln = l0.x, l1 = l0.y, l2 = l0.z;  // impulses of the contact being updated
+#pragma unroll 1
+        for (int k = 0; k < nc; ++k) {
+          const int r = 3 * k;
+          // this contact's constants and this lane's row of A in its columns
+          // (loaded first, used after the shuffles), the next one's impulses
+          const float4 c0 = cS[2 * k], c1 = cS[2 * k + 1];
+          const float an = sm.Yt[r][lane], a1 = sm.Yt[r + 1][lane], a2 = sm.Yt[r + 2][lane];
+          const float4 nl = lamS[k + 1];
+          const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
+          const float gn = fmaf(c0.y, ln, wn);
+          const float lnn = fmaxf(0.f, fmaf(-gn, c0.x, ln));
+          const float dn = lnn - ln;
+          const float wd = fmaf(an, dn, w);
+          const float g1 = fmaf(c1.z, dn, fmaf(c0.w, l1, w1));
+          const float g2 = fmaf(c1.w, dn, fmaf(c1.y, l2, w2));
+          float l1t = fmaf(-g1, c0.z, l1);
+          float l2t = fmaf(-g2, c1.x, l2);
+          const float lim = P.mu * lnn;
+          const float nt2 = l1t * l1t + l2t * l2t;
+          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+          l1t *= sc;
+          l2t *= sc;
+          w = fmaf(a2, l2t - l2, fmaf(a1, l1t - l1, wd));
+          lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
+          ln = nl.x;
+          l1 = nl.y;
+          l2 = nl.z;
+        }
       }
       __syncwarp();
       // u = sum_r Y_r lam_r (lane = dof)
+#pragma unroll 1
       for (int kk = 0; kk < nc; ++kk) {
         const float4 l4 = lamS[kk];
         const float* Yk = Yg + (size_t)(3 * kk) * 32 + lane;
@@ -940,73 +1052,12 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         lam_a[0] = l4.x; lam_a[1] = l4.y; lam_a[2] = l4.z;
       }
     } else if (nc > 0) {
-      // Dof space (lane = dof, u = L^T (v - v_free)), one contact of
-      // lookahead: the next contact's row products are reduced over the warp
-      // from u before the current update lands, then brought up to date with
-      // B_k (u changes by Y_k^T dlam_k), so that the five-level reduction
-      // runs beside the update instead of ahead of it.  Contact impulses sit
-      // in shared memory: every lane computes and stores them alike and reads
-      // back its own writes.
       float4* lamS = reinterpret_cast<float4*>(&sm.R[0][0]);
-      for (int k0 = lane; k0 < nc; k0 += 32) lamS[k0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      __syncwarp();
-      const float4* c4 = reinterpret_cast<const float4*>(cstg);
-      // more than 10 contacts here: the next contact is never the current one
-      int k = 0, kn = 1;
-      float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
-      const float* Zn = Yg + (size_t)(3 * kn) * 32;
-      float z0 = Zn[lane], z1 = Zn[32 + lane], z2 = Zn[64 + lane];
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // Y_k . u before update k (u = 0 at the start)
-      float ln = 0.f, l1 = 0.f, l2 = 0.f;  // impulses of contact k
-      const int nupd = P.iters * nc;
-      for (int upd = 0; upd < nupd; ++upd) {
-        const int knn = (kn + 1 < nc) ? kn + 1 : 0;
-        // this contact's constants and coupling block B_k (loaded first, used
-        // after the reduction's shuffles); the next one's impulses and the
-        // rows after it
-        const float4 ca = c4[6 * k], cb4 = c4[6 * k + 1], cc4 = c4[6 * k + 2];
-        const float4 bq0 = c4[6 * k + 3], bq1 = c4[6 * k + 4], bq2 = c4[6 * k + 5];
-        const float4 nl = lamS[kn];
-        const float* Zz = Yg + (size_t)(3 * knn) * 32;
-        const float zz0 = Zz[lane], zz1 = Zz[32 + lane], zz2 = Zz[64 + lane];
-        // the next contact's row products against u before this update
-        float p0 = z0 * u, p1 = z1 * u, p2 = z2 * u;
-        warp_sum3(p0, p1, p2, lane);
-        // constants: (b_n, inv_n, R_n, b_t1), (inv_t1, R_t1, b_t2, inv_t2), (R_t2, A_t1n, A_t2n, 0)
-        const float gn = s0 + ca.x + ca.z * ln;
-        const float lnn = fmaxf(0.f, ln - gn * ca.y);
-        const float dn = lnn - ln;
-        const float g1 = s1 + cc4.y * dn + ca.w + cb4.y * l1;
-        const float g2 = s2 + cc4.z * dn + cb4.z + cc4.x * l2;
-        float l1t = l1 - g1 * cb4.x;
-        float l2t = l2 - g2 * cb4.w;
-        const float lim = P.mu * lnn;
-        const float nt2 = l1t * l1t + l2t * l2t;
-        const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
-        l1t *= sc;
-        l2t *= sc;
-        const float d1 = l1t - l1, d2 = l2t - l2;
-        u += y0 * dn + y1 * d1 + y2 * d2;
-        lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
-        // B_k row-major in bq0..bq2: (b00 b01 b02 b10) (b11 b12 b20 b21) (b22 ...)
-        s0 = p0 + bq0.x * dn + bq0.y * d1 + bq0.z * d2;
-        s1 = p1 + bq0.w * dn + bq1.x * d1 + bq1.y * d2;
-        s2 = p2 + bq1.z * dn + bq1.w * d1 + bq2.x * d2;
-        ln = nl.x;
-        l1 = nl.y;
-        l2 = nl.z;
-        y0 = z0; y1 = z1; y2 = z2;
-        z0 = zz0; z1 = zz1; z2 = zz2;
-        k = kn;
-        kn = knn;
-      }
-      __syncwarp();
-      {
-        const float4 la = lane < nc ? lamS[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 lb = lane + 32 < nc ? lamS[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-        lam_a[0] = la.x; lam_a[1] = la.y; lam_a[2] = la.z;
-        lam_b[0] = lb.x; lam_b[1] = lb.y; lam_b[2] = lb.z;
-      }
+      u = dof_space_sweep(lamS, cstg, Yg, nc, P.iters, P.mu, lane);
+      const float4 la = lane < nc ? lamS[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 lb = lane + 32 < nc ? lamS[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+      lam_a[0] = la.x; lam_a[1] = la.y; lam_a[2] = la.z;
+      lam_b[0] = lb.x; lam_b[1] = lb.y; lam_b[2] = lb.z;
     }
     float vplus = vfree + upper_solve(sm, u, nv, lane);
     if (lane >= nv) vplus = 0.f;
