@@ -115,7 +115,8 @@ typedef struct {
     int32_t device;           /* CUDA device ordinal                         */
     uint64_t stream;          /* cudaStream_t or 0                           */
     int32_t steps_per_launch; /* persistent chunk; 0: library default (5000) */
-    int32_t warps_per_block;  /* 0: autotuned default                        */
+    int32_t warps_per_block;  /* 1, 2, 4 or 8; 0: sim_autotune's choice,
+                                 1 until it runs                             */
     float min_cfm;            /* floor of a contact row's softness R [1/kg]:
                                  R = max(kappa A, min_cfm); bounds the
                                  impulse of rows the dofs can barely move    */

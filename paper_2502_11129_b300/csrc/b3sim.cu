@@ -80,7 +80,10 @@ struct sim_ctx {
   // short ones (a sum over launches of maxima): 5000-step launches measured
   // 16 % faster than 500-step ones on 4096 grammar robots.
   int steps_per_launch = kDefaultStepsPerLaunch;
-  int wpb = 4;
+  // one warp per block: the compiler then knows a block is one warp, and
+  // the code of that instance is the smallest (the step is bound by
+  // instruction fetch)
+  int wpb = 1;
   bool lock = false;  // phase-locked launches (warps of a block in step)
   int wpsm = 16;      // resident warps per SM the kernel's registers are sized for
   std::map<long long, cudaGraphExec_t> graphs;
@@ -705,7 +708,7 @@ int sim_step_n_noalloc(const sim_config* cfg, const sim_device_population* pop, 
                     nullptr,      nullptr,      pop->n,   make_params(cfg), stream, 0,
                     0,            nullptr,      nullptr,  nullptr,     nullptr,    nullptr,   nullptr,
                     nullptr,      nullptr,      nullptr};
-    const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 4;
+    const int wpb = cfg->warps_per_block > 0 ? cfg->warps_per_block : 1;
     const int wpsm = cfg->warps_per_sm > 0 ? cfg->warps_per_sm : 16;
     const int spl = cfg->steps_per_launch > 0 ? cfg->steps_per_launch : kDefaultStepsPerLaunch;
     e = enqueue_launches(args, n_steps, wpb, cfg->phase_lock == 1, wpsm, spl);

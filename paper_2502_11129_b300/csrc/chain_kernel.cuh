@@ -735,7 +735,7 @@ chain_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const uns
           float l2t = l2 - g2 * cs[7];
           const float lim = P.mu * lnn;
           const float nt2 = l1t * l1t + l2t * l2t;
-          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+          const float sc = fminf(1.f, lim * rsqrt_ftz(nt2));
           l1t *= sc;
           l2t *= sc;
           const float d1 = l1t - l1, d2 = l2t - l2;

@@ -9,16 +9,19 @@
 //   * lane = body    for the tree passes (FK, velocities, inertias, CPG);
 //   * lane = field   for the leaf-to-root accumulations (one lane per spatial
 //                    force / inertia component, serial over bodies);
-//   * lane = row     for the Cholesky trailing update;
-//   * lane = dof     for the triangular solves and the Gauss-Seidel sweeps;
-//   * lane = contact for building contact Jacobian rows;
+//   * lane = row     for the Cholesky columns, the contact Jacobian rows and
+//                    the Gauss-Seidel sweep of up to 10 contacts;
+//   * lane = contact for the sweep of 11 to 32 contacts;
+//   * lane = dof     for the triangular solves and the sweep of more;
 //   * lane = pair    for the box/box broad and narrow phases.
 //
-// Gauss-Seidel runs in the Cholesky-transformed velocity u = L^T (v - v_free):
-// with Y_r = L^-1 J_r^T, the row residual J_r v = J_r v_free + Y_r . u and the
-// update v += M^-1 J_r^T dl is u += Y_r dl.  This is the same iteration as
-// sweeping in v (identical in exact arithmetic), with one nv-vector per row
-// instead of two.  After the sweeps v+ = v_free + L^-T u.
+// Gauss-Seidel works with Y_r = L^-1 J_r^T: the row residual J_r v =
+// J_r v_free + Y_r . u with u = L^T (v - v_free), and the update
+// v += M^-1 J_r^T dl is u += Y_r dl.  Up to 32 contacts the sweep runs in
+// contact space on the residuals themselves (w += A_r. dl with the Delassus
+// matrix A = Y Y^T), beyond in dof space on u; both are the iteration of
+// sweeping in v (identical in exact arithmetic).  After the sweeps
+// v+ = v_free + L^-T u.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,14 +37,19 @@ constexpr unsigned kFull = 0xffffffffu;
 // contact (kCstG floats: b, 1/(A+R), R of its three rows, the normal-tangent
 // couplings A_t1n, A_t2n, a zero, then the 3 x 3 block B_k = Y_(k+1) Y_k^T
 // that couples it to the next contact of the sweep, row-major, and three
-// zeros), then the last step's v_free and impulses (inspection only)
+// zeros), the last step's v_free and impulses (inspection only), then the
+// Delassus matrix of the lane-per-contact sweep (up to kLaneContacts^2 blocks
+// of 3 x 3 floats, 12 apart)
 constexpr int kCstG = 24;
+constexpr int kLaneContacts = 32;  // lane-per-contact sweeps up to this many contacts
 constexpr size_t kStageOffset = (size_t)kCand * kCandW;            // 32 lanes x 8 points x 8 floats
 constexpr size_t kYOffset = kStageOffset + (size_t)32 * 8 * kCandW;
 constexpr size_t kCstOffset = kYOffset + (size_t)kYRows * 32;
 constexpr size_t kDbgOffset = kCstOffset + (size_t)kCapMax * kCstG;
 constexpr int kPhases = 10;  // per-phase cycle counters (inspection only)
-constexpr size_t kScratchFloats = kDbgOffset + 32 + 4 * kCapMax + 16;
+constexpr size_t kAOffset = kDbgOffset + 32 + 4 * kCapMax + 16;
+constexpr size_t kScratchFloats = kAOffset + (size_t)kLaneContacts * kLaneContacts * 12;
+static_assert(kAOffset % 4 == 0 && kScratchFloats % 4 == 0, "float4 rows of the scratch stay aligned");
 
 struct __align__(16) WarpSmem {
   float R[9][32];          // body rotations (lane = body)
@@ -72,6 +80,17 @@ struct __align__(16) WarpSmem {
 static_assert(16 * (sizeof(WarpSmem) + 1024) <= 164 * 1024, "per-warp shared memory");
 
 __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFull, x, src); }
+
+// 1/sqrt(x) from the special-function unit with subnormals flushed to zero
+// (PTX rsqrt.approx.ftz.f32, a few ulp): without the flush the compiler adds
+// a subnormal fix-up, which lengthens the Gauss-Seidel update's dependency
+// chain by ~15 cycles.  Used for the friction-disk scale min(1, mu l_n / |l_t|),
+// where a flushed |l_t|^2 < 1e-38 changes nothing measurable.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // Double-float arithmetic (Dekker 1971 products, Knuth two-sum): a value is
 // h + l in FP32 with |l| <= ulp(h) / 2, about 44 bits.  The round-to-nearest
@@ -204,7 +223,122 @@ static __device__ __noinline__ void keep_deepest(float* cand, int ncand, int cap
   }
 }
 
-// Gauss-Seidel sweeps of more than 10 contacts in dof space; returns u (this
+// Gauss-Seidel sweeps of 11 to kLaneContacts contacts in contact space,
+// lane c = contact c: the lane keeps the residuals w = J v_free - bias +
+// A lam of its contact's three rows, their impulses and their constants in
+// registers.  Every lane forms the update of its own contact from its own
+// residuals; the sweep takes lane k's, broadcast with three shuffles, and
+// every lane adds A_(c,k) dlam_k to its residuals, reading its 3 x 3 block of
+// the Delassus matrix A = Y Y^T from the global scratch (built here, blocks
+// prefetched two updates ahead).  The same iteration as the dof-space sweep;
+// the update's dependency chain has one shuffle and no warp reduction.
+// Returns u (this lane's dof) and leaves every contact's impulses in lamS.
+static __device__ __noinline__ float lane_contact_sweep(float4* lamS, const float* __restrict__ cstg,
+                                                        const float* __restrict__ Yg, float* __restrict__ Ag,
+                                                        int nc, int nv, int iters, float mu, int lane) {
+  // A = Y Y^T, lane = row r: block (k, c) (rows of contact c, columns of
+  // contact k) at Ag + (k nc + c) 12, row-major 3 x 3 with 3 floats of padding
+  const int nr = 3 * nc;
+#pragma unroll 1
+  for (int r0 = 0; r0 < nr; r0 += 32) {
+    const int r = r0 + lane;
+    const bool act = r < nr;
+    float y[32];
+    {
+      const float4* Yr = reinterpret_cast<const float4*>(Yg + (size_t)(act ? r : 0) * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 t = Yr[q];
+        y[4 * q] = t.x; y[4 * q + 1] = t.y; y[4 * q + 2] = t.z; y[4 * q + 3] = t.w;
+      }
+    }
+    const int c = r / 3;
+    float* dst = Ag + (size_t)c * 12 + 3 * (r - 3 * c);
+    int ks = 0, ds = 0;  // column s = 3 ks + ds
+#pragma unroll 1
+    for (int s = 0; s < nr; ++s) {
+      const float4* Ys = reinterpret_cast<const float4*>(Yg + (size_t)s * 32);
+      float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        if (4 * q < nv) {
+          const float4 t = Ys[q];
+          acc0 = fmaf(y[4 * q], t.x, fmaf(y[4 * q + 1], t.y, fmaf(y[4 * q + 2], t.z, fmaf(y[4 * q + 3], t.w, acc0))));
+        }
+        if (4 * q + 4 < nv) {
+          const float4 t = Ys[q + 1];
+          acc1 = fmaf(y[4 * q + 4], t.x, fmaf(y[4 * q + 5], t.y, fmaf(y[4 * q + 6], t.z, fmaf(y[4 * q + 7], t.w, acc1))));
+        }
+      }
+      if (act) dst[(size_t)ks * nc * 12 + ds] = acc0 + acc1;
+      if (++ds == 3) {
+        ds = 0;
+        ++ks;
+      }
+    }
+  }
+  // this lane's contact: residuals (from J v_free - bias), impulses and, with
+  // g = 1/(A+R), a = 1 - R g, b = g A_tn: (g_n, a_n, g_t1, a_t1, b_t1, g_t2, a_t2, b_t2)
+  const bool mine = lane < nc;
+  float wn = 0.f, w1 = 0.f, w2 = 0.f;
+  float gn = 0.f, an = 1.f, g1 = 0.f, a1 = 1.f, b1 = 0.f, g2 = 0.f, a2 = 1.f, b2 = 0.f;
+  if (mine) {
+    const float4* c4 = reinterpret_cast<const float4*>(cstg) + 6 * lane;
+    // (b_n, g_n, R_n, b_t1), (g_t1, R_t1, b_t2, g_t2), (R_t2, A_t1n, A_t2n, 0)
+    const float4 x0 = c4[0], x1 = c4[1], x2 = c4[2];
+    wn = x0.x; gn = x0.y; an = fmaf(-x0.z, x0.y, 1.f); w1 = x0.w;
+    g1 = x1.x; a1 = fmaf(-x1.y, x1.x, 1.f); b1 = x1.x * x2.y;
+    w2 = x1.z; g2 = x1.w; a2 = fmaf(-x2.x, x1.w, 1.f); b2 = x1.w * x2.z;
+  }
+  __syncwarp();  // the blocks written above are read by other lanes
+  float ln = 0.f, l1 = 0.f, l2 = 0.f;
+  const float4* A4 = reinterpret_cast<const float4*>(Ag) + 3 * lane;
+  const int kstride = 3 * nc;  // float4 between block rows k and k + 1
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // blocks of the current contact and the next one (prefetch distance 2)
+  float4 p0 = mine ? A4[0] : z4, p1 = mine ? A4[1] : z4, p2 = mine ? A4[2] : z4;
+  float4 q0 = mine ? A4[kstride] : z4, q1 = mine ? A4[kstride + 1] : z4, q2 = mine ? A4[kstride + 2] : z4;
+  const int nupd = iters * nc;
+  int k = 0, k2 = 2;  // contact of this update, and of the block loaded now
+#pragma unroll 1
+  for (int upd = 0; upd < nupd; ++upd) {
+    const float4* An = A4 + (size_t)kstride * k2;
+    const float4 r0 = mine ? An[0] : z4, r1 = mine ? An[1] : z4, r2 = mine ? An[2] : z4;
+    const float lnn = fmaxf(0.f, fmaf(-gn, wn, an * ln));
+    const float dn = lnn - ln;
+    const float l1t = fmaf(-b1, dn, fmaf(-g1, w1, a1 * l1));
+    const float l2t = fmaf(-b2, dn, fmaf(-g2, w2, a2 * l2));
+    const float sc = fminf(1.f, (mu * lnn) * rsqrt_ftz(fmaf(l1t, l1t, l2t * l2t)));
+    const float d1 = fmaf(l1t, sc, -l1), d2 = fmaf(l2t, sc, -l2);
+    const float Dn = shf(dn, k), D1 = shf(d1, k), D2 = shf(d2, k);
+    if (lane == k) {
+      ln = lnn;
+      l1 = l1t * sc;
+      l2 = l2t * sc;
+    }
+    // block (k, lane) row-major in p0..p2: (a00 a01 a02 a10) (a11 a12 a20 a21) (a22 . . .)
+    wn = fmaf(p0.z, D2, fmaf(p0.y, D1, fmaf(p0.x, Dn, wn)));
+    w1 = fmaf(p1.y, D2, fmaf(p1.x, D1, fmaf(p0.w, Dn, w1)));
+    w2 = fmaf(p2.x, D2, fmaf(p1.w, D1, fmaf(p1.z, Dn, w2)));
+    p0 = q0; p1 = q1; p2 = q2;
+    q0 = r0; q1 = r1; q2 = r2;
+    k = k + 1 < nc ? k + 1 : 0;
+    k2 = k2 + 1 < nc ? k2 + 1 : 0;
+  }
+  if (mine) lamS[lane] = make_float4(ln, l1, l2, 0.f);
+  __syncwarp();
+  // u = sum_r Y_r lam_r (lane = dof)
+  float u = 0.f;
+#pragma unroll 1
+  for (int kk = 0; kk < nc; ++kk) {
+    const float4 l4 = lamS[kk];
+    const float* Yk = Yg + (size_t)(3 * kk) * 32 + lane;
+    u += l4.x * Yk[0] + l4.y * Yk[32] + l4.z * Yk[64];
+  }
+  return u;
+}
+
+// Gauss-Seidel sweeps of more than kLaneContacts contacts in dof space; returns u (this
 // lane's dof) and leaves every contact's impulses in lamS.  Out of line, so
 // that its code sits outside the step loop that most robots run.
 static __device__ __noinline__ float dof_space_sweep(float4* lamS, const float* __restrict__ cstg,
@@ -221,7 +355,7 @@ static __device__ __noinline__ float dof_space_sweep(float4* lamS, const float* 
   for (int k0 = lane; k0 < nc; k0 += 32) lamS[k0] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
   const float4* c4 = reinterpret_cast<const float4*>(cstg);
-  // more than 10 contacts here: the next contact is never the current one
+  // more than kLaneContacts contacts here: the next contact is never the current one
   int k = 0, kn = 1;
   float y0 = Yg[lane], y1 = Yg[32 + lane], y2 = Yg[64 + lane];
   const float* Zn = Yg + (size_t)(3 * kn) * 32;
@@ -254,7 +388,7 @@ static __device__ __noinline__ float dof_space_sweep(float4* lamS, const float* 
     float l2t = l2 - g2 * cb4.w;
     const float lim = mu * lnn;
     const float nt2 = l1t * l1t + l2t * l2t;
-    const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
+    const float sc = fminf(1.f, lim * rsqrt_ftz(nt2));
     l1t *= sc;
     l2t *= sc;
     const float d1 = l1t - l1, d2 = l2t - l2;
@@ -707,11 +841,18 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         return f2_add(f2_add(two_sum(p0z, -drop), hzb), hl);
       };
       auto below = [](f2 h) { return h.h < 0.f || (h.h == 0.f && h.l < 0.f); };
+      // the depths of the vertices below the plane wait in the (free)
+      // accumulator rows until their candidate slots are known
       if (body) {
         const int nvert = sph ? 1 : 8;
 #pragma unroll 1
-        for (int k = 0; k < nvert; ++k)
-          if (below(vheight(k))) mask8 |= 1u << k;
+        for (int k = 0; k < nvert; ++k) {
+          const f2 vh = vheight(k);
+          if (below(vh)) {
+            mask8 |= 1u << k;
+            sm.acc[k][lane] = -(vh.h + vh.l);
+          }
+        }
       }
       const int cnt = __popc(mask8);
       int incl = cnt;
@@ -730,10 +871,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
 #pragma unroll
         for (int a = 0; a < 3; ++a) pr[a] = r[a] + (R[3 * a] * l0 + R[3 * a + 1] * l1 + R[3 * a + 2] * l2);
         pr[2] -= drop;
-        if (off < kCand) {
-          const f2 vh = vheight(k);
-          put_candidate(cand, off, pr, up, -(vh.h + vh.l), lane, 255);
-        }
+        if (off < kCand) put_candidate(cand, off, pr, up, sm.acc[k][lane], lane, 255);
         ++off;
       }
       ncand = shfi(incl, 31);
@@ -899,7 +1037,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     // tangent/normal coupling A_tn = Y_t . Y_n of each contact (lane =
     // contact), and for the dof-space sweep (more than 10 contacts) the block
     // B_k = Y_(k+1) Y_k^T to the next contact in sweep order
-    const bool dofspace = 3 * nc > 32;
+    const bool dofspace = nc > kLaneContacts;
 #pragma unroll 1
     for (int k0 = 0; k0 < nc; k0 += 32) {
       const int k = k0 + lane;
@@ -987,17 +1125,21 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         __syncwarp();
       }
       // Staging in the rotation rows of shared memory (free during the
-      // sweep): the Gauss-Seidel constants of every contact, two float4
-      // (1/(A+R)_n, R_n, 1/(A+R)_t1, R_t1), (1/(A+R)_t2, R_t2, A_t1n, A_t2n),
-      // and the impulses of every contact, which all lanes compute alike and
-      // store alike, so each lane later reads back its own write.
+      // sweep): the Gauss-Seidel constants of every contact and the
+      // impulses of every contact, which all lanes compute alike and store
+      // alike, so each lane later reads back its own write.  With
+      // g = 1/(A+R), a = 1 - R g (= A g) and b = g A_tn, a row's projected
+      // update l - g (w + R l + A_tn dn) is a l - g w - b dn: the terms
+      // known before the normal update leave the dependency chain.  Per
+      // contact (g_n, a_n, g_t1, a_t1), (b_t1, g_t2, a_t2, b_t2).
       float4* lamS = reinterpret_cast<float4*>(&sm.R[0][0]);
       float4* cS = lamS + 12;
       if (lane < nc) {
         const float4* c4 = reinterpret_cast<const float4*>(cstg) + 6 * lane;
+        // (b_n, g_n, R_n, b_t1), (g_t1, R_t1, b_t2, g_t2), (R_t2, A_t1n, A_t2n, 0)
         const float4 x0 = c4[0], x1 = c4[1], x2 = c4[2];
-        cS[2 * lane] = make_float4(x0.y, x0.z, x1.x, x1.y);
-        cS[2 * lane + 1] = make_float4(x1.w, x2.x, x2.y, x2.z);
+        cS[2 * lane] = make_float4(x0.y, fmaf(-x0.z, x0.y, 1.f), x1.x, fmaf(-x1.y, x1.x, 1.f));
+        cS[2 * lane + 1] = make_float4(x1.x * x2.y, x1.w, fmaf(-x2.x, x1.w, 1.f), x1.w * x2.z);
         lamS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
@@ -1019,21 +1161,17 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           const float an = sm.Yt[r][lane], a1 = sm.Yt[r + 1][lane], a2 = sm.Yt[r + 2][lane];
           const float4 nl = lamS[k + 1];
           const float wn = shf(w, r), w1 = shf(w, r + 1), w2 = shf(w, r + 2);
-          const float gn = fmaf(c0.y, ln, wn);
-          const float lnn = fmaxf(0.f, fmaf(-gn, c0.x, ln));
+          const float lnn = fmaxf(0.f, fmaf(-c0.x, wn, c0.y * ln));
           const float dn = lnn - ln;
           const float wd = fmaf(an, dn, w);
-          const float g1 = fmaf(c1.z, dn, fmaf(c0.w, l1, w1));
-          const float g2 = fmaf(c1.w, dn, fmaf(c1.y, l2, w2));
-          float l1t = fmaf(-g1, c0.z, l1);
-          float l2t = fmaf(-g2, c1.x, l2);
-          const float lim = P.mu * lnn;
-          const float nt2 = l1t * l1t + l2t * l2t;
-          const float sc = nt2 > lim * lim ? lim * rsqrtf(nt2) : 1.f;
-          l1t *= sc;
-          l2t *= sc;
-          w = fmaf(a2, l2t - l2, fmaf(a1, l1t - l1, wd));
-          lamS[k] = make_float4(lnn, l1t, l2t, 0.f);
+          const float p1 = fmaf(-c0.z, w1, c0.w * l1), p2 = fmaf(-c1.y, w2, c1.z * l2);
+          const float l1t = fmaf(-c1.x, dn, p1), l2t = fmaf(-c1.w, dn, p2);
+          // disk cone |l_t| <= mu l_n: scale down when outside (rsqrt(0) =
+          // inf gives a factor of 1, or 0 when l_n = 0)
+          const float sc = fminf(1.f, (P.mu * lnn) * rsqrt_ftz(fmaf(l1t, l1t, l2t * l2t)));
+          const float d1 = fmaf(l1t, sc, -l1), d2 = fmaf(l2t, sc, -l2);
+          w = fmaf(a2, d2, fmaf(a1, d1, wd));
+          lamS[k] = make_float4(lnn, l1t * sc, l2t * sc, 0.f);
           ln = nl.x;
           l1 = nl.y;
           l2 = nl.z;
@@ -1053,7 +1191,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
     } else if (nc > 0) {
       float4* lamS = reinterpret_cast<float4*>(&sm.R[0][0]);
-      u = dof_space_sweep(lamS, cstg, Yg, nc, P.iters, P.mu, lane);
+      u = nc <= kLaneContacts ? lane_contact_sweep(lamS, cstg, Yg, cand + kAOffset, nc, nv, P.iters, P.mu, lane)
+                              : dof_space_sweep(lamS, cstg, Yg, nc, P.iters, P.mu, lane);
       const float4 la = lane < nc ? lamS[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 lb = lane + 32 < nc ? lamS[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
       lam_a[0] = la.x; lam_a[1] = la.y; lam_a[2] = la.z;
