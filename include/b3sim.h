@@ -278,10 +278,11 @@ int sim_debug_sincos(const double* x, int32_t n, double* s, double* c);
  * sim_step_n_noalloc advances n variants that the CALLER keeps in device
  * memory it already owns.  It calls no cudaMalloc, cudaFree or allocating
  * library routine.  Its per-variant scratch (contact candidates, narrow-phase
- * staging rows, contact Jacobian rows and Gauss-Seidel constants, about 48 KB
- * per variant) is a fixed array inside this library: SIM_NOALLOC_MAX_VARIANTS
- * variants, about 3.1 MB, held by every device that loads the library until
- * the process exits.  Larger n is rejected with SIM_EINVAL.
+ * staging rows, contact Jacobian rows, Gauss-Seidel constants and a Delassus
+ * matrix of up to 32 contacts, about 95 KB per variant) is a fixed array
+ * inside this library: SIM_NOALLOC_MAX_VARIANTS variants, about 6 MB, held by
+ * every device that loads the library until the process exits.  Larger n
+ * is rejected with SIM_EINVAL.
  *   - cfg->device is made current; cfg->stream (0: the legacy default
  *     stream) receives the work, asynchronously.
  *   - The first call on a device looks up the scratch's device address

@@ -237,7 +237,9 @@ static __device__ __noinline__ float lane_contact_sweep(float4* lamS, const floa
                                                         const float* __restrict__ Yg, float* __restrict__ Ag,
                                                         int nc, int nv, int iters, float mu, int lane) {
   // A = Y Y^T, lane = row r: block (k, c) (rows of contact c, columns of
-  // contact k) at Ag + (k nc + c) 12, row-major 3 x 3 with 3 floats of padding
+  // contact k) at Ag + (k nc + c) 12, row-major 3 x 3 with 3 floats of
+  // padding.  A is symmetric: lane r forms A_rs for s >= r and writes it to
+  // both places, so a pass of 32 rows starts at its own first row.
   const int nr = 3 * nc;
 #pragma unroll 1
   for (int r0 = 0; r0 < nr; r0 += 32) {
@@ -252,11 +254,12 @@ static __device__ __noinline__ float lane_contact_sweep(float4* lamS, const floa
         y[4 * q] = t.x; y[4 * q + 1] = t.y; y[4 * q + 2] = t.z; y[4 * q + 3] = t.w;
       }
     }
-    const int c = r / 3;
-    float* dst = Ag + (size_t)c * 12 + 3 * (r - 3 * c);
-    int ks = 0, ds = 0;  // column s = 3 ks + ds
+    const int c = r / 3, dr = r - 3 * c;
+    float* dst = Ag + (size_t)c * 12 + 3 * dr;    // A_rs: block (ks, c), entry (dr, ds)
+    float* mir = Ag + (size_t)c * nc * 12 + dr;   // A_sr: block (c, ks), entry (ds, dr)
+    int ks = r0 / 3, ds = r0 - 3 * ks;  // column s = 3 ks + ds
 #pragma unroll 1
-    for (int s = 0; s < nr; ++s) {
+    for (int s = r0; s < nr; ++s) {
       const float4* Ys = reinterpret_cast<const float4*>(Yg + (size_t)s * 32);
       float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
@@ -270,7 +273,11 @@ static __device__ __noinline__ float lane_contact_sweep(float4* lamS, const floa
           acc1 = fmaf(y[4 * q + 4], t.x, fmaf(y[4 * q + 5], t.y, fmaf(y[4 * q + 6], t.z, fmaf(y[4 * q + 7], t.w, acc1))));
         }
       }
-      if (act) dst[(size_t)ks * nc * 12 + ds] = acc0 + acc1;
+      if (act && s >= r) {
+        const float a = acc0 + acc1;
+        dst[(size_t)ks * nc * 12 + ds] = a;
+        mir[(size_t)ks * 12 + 3 * ds] = a;
+      }
       if (++ds == 3) {
         ds = 0;
         ++ks;
