@@ -58,10 +58,26 @@ typedef struct {
 int sur_create(const sur_config* cfg, sur_ctx_t** out);
 int sur_destroy(sur_ctx_t* ctx);
 
-/* Encode n robots (arrays of 32 body slots per robot, body 0 = core) on the
- * GPU into X_out (n x 128 floats, host). */
-int sur_encode(sur_ctx_t* ctx, const int8_t* parent, const int8_t* face, const int8_t* rot,
-               const float* w_int, const float* w_cpl, const int32_t* n_bodies, int32_t n, float* X_out);
+/* Encode n robots on the GPU into X_out (n x 128 floats, host): the bricks'
+ * zero-pose geometry and controller weights.  Per robot, arrays of 32 body
+ * slots (body 0 = the core, parent[b] < b): parent, hinge axis index in the
+ * body frame (0..2), joint frame R_fix (9 floats, row-major) and p_fix (3,
+ * metres) in the parent frame, box centre in the body frame (3, metres), CPG
+ * weight and coupling weight (to the parent's hinge); n_bodies in 1..21.
+ * Joint frames are taken on the integer millimetre lattice the robots are
+ * built on: R_fix rounded to its integer entries (a signed permutation),
+ * offsets and centres rounded to whole millimetres.  Zero-pose kinematics
+ * then place every brick exactly; the bricks are ordered by box centre in
+ * the core frame (z, then x, then y) and brick i fills columns 6i .. 6i+5
+ * with (x, y, z) / 256 mm, its hinge axis code (1, 2, 3: along the core's
+ * x, y, z) / 3, its CPG weight, and its coupling weight (0 when its parent
+ * is the core); columns 120..127 and unused slots are zero.  A paper-silent
+ * reading: the paper defines no encoding.  Returns SUR_EINVAL on NULL
+ * arrays, n < 1, n_bodies outside 1..21, a parent not before its child or
+ * an axis outside 0..2. */
+int sur_encode(sur_ctx_t* ctx, const int8_t* parent, const int8_t* axis, const float* R_fix, const float* p_fix,
+               const float* box_center, const float* w_int, const float* w_cpl, const int32_t* n_bodies, int32_t n,
+               float* X_out);
 
 /* Train `epochs` passes over (X, y) (n x 128, n) in shuffled mini-batches of
  * `batch` (1..SUR_MAX_BATCH).  Targets are standardised with their mean and

@@ -6,9 +6,11 @@ module; it shares no code with the CUDA surrogate library.
 What it computes, plainly (the paper's EA context, Sec. 1: memetic / Lamarckian
 evolution of robot morphologies and controllers, where evaluations are
 simulations):
-  * encode   -- a robot genotype as a 128-d vector: 20 brick slots x
-                (present, parent / 20, face / 5, rotation / 3, CPG weight),
-                then the 19 coupling weights of bricks 2..20, zero padding;
+  * encode   -- a robot as a 128-d vector: its bricks' zero-pose geometry
+                and controller weights, 20 slots of 6 (centre x, y, z in the
+                core frame in millimetres / 256, hinge-axis code / 3, CPG
+                weight, coupling weight to the parent hinge), bricks ordered
+                by centre (z, then x, then y), zero padding;
   * forward  -- y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 on BF16-rounded
                 weights and inputs, FP64 arithmetic;
   * loss     -- mean squared error on standardised targets;
@@ -39,26 +41,45 @@ def bf16_round(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def encode(parent, face, rot, w_int, w_cpl, nb) -> np.ndarray:
+def zero_pose_mm(parent, R_fix, p_fix, com, nb):
+    """Box centres and rotations of every body at zero hinge angles, in the
+    core frame, on the integer millimetre lattice: joint rotations rounded
+    to their integer entries, offsets to whole millimetres (exact for the
+    lattice-built robots).  Parents precede children."""
+    R = [np.eye(3, dtype=np.int64)]
+    o = [np.zeros(3, np.int64)]
+    c = [np.rint(np.asarray(com[0], np.float64) * 1000.0).astype(np.int64)]
+    for b in range(1, nb):
+        Rf = np.rint(np.asarray(R_fix[b], np.float64)).astype(np.int64).reshape(3, 3)
+        pf = np.rint(np.asarray(p_fix[b], np.float64) * 1000.0).astype(np.int64)
+        cb = np.rint(np.asarray(com[b], np.float64) * 1000.0).astype(np.int64)
+        Rp, op = R[parent[b]], o[parent[b]]
+        R.append(Rp @ Rf)
+        o.append(op + Rp @ pf)
+        c.append(o[b] + R[b] @ cb)
+    return R, c
+
+
+def encode(parent, axis, R_fix, p_fix, com, w_int, w_cpl, nb) -> np.ndarray:
     """128-d encoding of one robot (arrays indexed by body, body 0 = core)."""
+    R, c = zero_pose_mm(parent, R_fix, p_fix, com, nb)
+    rows = []
+    for b in range(1, nb):
+        a = R[b][:, int(axis[b])]  # hinge axis in the core frame: a signed unit vector
+        code = int(np.argmax(np.abs(a))) + 1
+        cpl = w_cpl[b] if parent[b] >= 1 else 0.0
+        rows.append(((int(c[b][2]), int(c[b][0]), int(c[b][1])),
+                     [c[b][0] / 256.0, c[b][1] / 256.0, c[b][2] / 256.0, code / 3.0, float(w_int[b]), float(cpl)]))
+    rows.sort(key=lambda r: r[0])
     x = np.zeros(IN_DIM)
-    for i in range(SLOTS):
-        b = i + 1
-        if b < nb:
-            x[5 * i + 0] = 1.0
-            x[5 * i + 1] = parent[b] / 20.0
-            x[5 * i + 2] = face[b] / 5.0
-            x[5 * i + 3] = rot[b] / 3.0
-            x[5 * i + 4] = w_int[b]
-    for i in range(SLOTS - 1):
-        b = i + 2
-        if b < nb:
-            x[100 + i] = w_cpl[b]
+    for i, (_, f) in enumerate(rows[:SLOTS]):
+        x[6 * i:6 * i + 6] = f
     return x
 
 
 def encode_population(pop) -> np.ndarray:
-    return np.stack([encode(pop.parent[i], pop.genome_face[i], pop.genome_rot[i], pop.w_int[i],
+    R9 = pop.R_fix.reshape(pop.n, pop.slots, 9)
+    return np.stack([encode(pop.parent[i], pop.axis[i], R9[i], pop.p_fix[i], pop.com[i], pop.w_int[i],
                             pop.w_cpl[i], int(pop.nb[i])) for i in range(pop.n)])
 
 

@@ -34,6 +34,9 @@ namespace {
 constexpr int IN = SUR_IN_DIM;
 constexpr int HID = SUR_HIDDEN;
 constexpr int NP = SUR_NPARAMS;
+constexpr int kEncSlots = 20;               // brick slots of the encoding
+constexpr int kEncBodies = kEncSlots + 1;   // core + bricks
+static_assert(6 * kEncSlots <= IN, "six features per brick slot");
 constexpr int OW1 = 0;
 constexpr int OB1 = OW1 + HID * IN;
 constexpr int OW2 = OB1 + HID;
@@ -479,29 +482,85 @@ __global__ void gather_rows(const float* __restrict__ X, const float* __restrict
 
 // genotype encoding: 20 brick slots x (present, parent/20, face/5, rot/3,
 // CPG weight), coupling weights of bricks 2..20, zeros
-__global__ void encode_kernel(const int8_t* __restrict__ parent, const int8_t* __restrict__ face,
-                              const int8_t* __restrict__ rot, const float* __restrict__ w_int,
-                              const float* __restrict__ w_cpl, const int* __restrict__ nbod, int n, float* X) {
-  const int r = blockIdx.x;
-  const int j = threadIdx.x;
-  if (r >= n || j >= IN) return;
-  const int nb = nbod[r];
-  float x = 0.f;
-  if (j < 100) {
-    const int i = j / 5, f = j % 5, b = i + 1;
-    if (b < nb) {
-      const long o = (long)r * 32 + b;
-      if (f == 0) x = 1.f;
-      else if (f == 1) x = (float)parent[o] / 20.f;
-      else if (f == 2) x = (float)face[o] / 5.f;
-      else if (f == 3) x = (float)rot[o] / 3.f;
-      else x = w_int[o];
+// Encoding of a robot (one thread per robot): zero-pose kinematics on the
+// integer millimetre lattice (joint rotations rounded to their integer
+// entries, offsets and box centres to whole millimetres; parents precede
+// children), the bricks ordered by box centre (z, then x, then y), then per
+// slot (x, y, z) / 256 mm, hinge-axis code (1 + index of the core-frame axis
+// it lies along) / 3, CPG weight, coupling weight to a parent hinge (0 on
+// the core); slots 20 and beyond, and columns 120..127, are zero.
+__global__ void __launch_bounds__(128) encode_kernel(const int8_t* __restrict__ parent,
+                                                     const int8_t* __restrict__ axis,
+                                                     const float* __restrict__ R_fix,
+                                                     const float* __restrict__ p_fix,
+                                                     const float* __restrict__ com,
+                                                     const float* __restrict__ w_int,
+                                                     const float* __restrict__ w_cpl,
+                                                     const int* __restrict__ nbod, int n, float* X) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  constexpr int B = kEncBodies;
+  const int nb = nbod[r];  // 1 .. kEncBodies (checked by the caller)
+  const long o = (long)r * 32;
+  int R[B][9], org[B][3], cen[B][3];
+  unsigned long long key[B];
+  int idx[B];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) R[0][t] = (t % 4 == 0) ? 1 : 0;
+  org[0][0] = org[0][1] = org[0][2] = 0;
+  int nbr = 0;
+#pragma unroll 1
+  for (int b = 1; b < nb; ++b) {
+    const int p = parent[o + b];
+    int Rf[9], pf[3], cb[3];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) Rf[t] = (int)rintf(R_fix[(o + b) * 9 + t]);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      pf[t] = (int)rintf(p_fix[(o + b) * 3 + t] * 1000.f);
+      cb[t] = (int)rintf(com[(o + b) * 3 + t] * 1000.f);
     }
-  } else if (j < 119) {
-    const int b = j - 100 + 2;
-    if (b < nb) x = w_cpl[(long)r * 32 + b];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        R[b][3 * i + j] = R[p][3 * i] * Rf[j] + R[p][3 * i + 1] * Rf[3 + j] + R[p][3 * i + 2] * Rf[6 + j];
+      org[b][i] = org[p][i] + R[p][3 * i] * pf[0] + R[p][3 * i + 1] * pf[1] + R[p][3 * i + 2] * pf[2];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      cen[b][i] = org[b][i] + R[b][3 * i] * cb[0] + R[b][3 * i + 1] * cb[1] + R[b][3 * i + 2] * cb[2];
+    // lexicographic (z, x, y), each offset into 13 bits (|coordinate| < 4096 mm)
+    const unsigned long long k = ((unsigned long long)(cen[b][2] + 4096) << 26) |
+                                 ((unsigned long long)(cen[b][0] + 4096) << 13) |
+                                 (unsigned long long)(cen[b][1] + 4096);
+    // insertion into the sorted list of the bricks so far
+    int pos = nbr;
+    while (pos > 0 && key[pos - 1] > k) {
+      key[pos] = key[pos - 1];
+      idx[pos] = idx[pos - 1];
+      --pos;
+    }
+    key[pos] = k;
+    idx[pos] = b;
+    ++nbr;
   }
-  X[(long)r * IN + j] = x;
+  float* x = X + (long)r * IN;
+#pragma unroll 1
+  for (int j = 0; j < IN; ++j) x[j] = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < nbr && i < kEncSlots; ++i) {
+    const int b = idx[i];
+    const int ax = axis[o + b];
+    // column ax of R_b is the hinge axis, a signed unit vector along x, y or z
+    const int code = (R[b][ax] != 0) ? 1 : ((R[b][3 + ax] != 0) ? 2 : 3);
+    x[6 * i + 0] = (float)cen[b][0] / 256.f;
+    x[6 * i + 1] = (float)cen[b][1] / 256.f;
+    x[6 * i + 2] = (float)cen[b][2] / 256.f;
+    x[6 * i + 3] = (float)code / 3.f;
+    x[6 * i + 4] = w_int[o + b];
+    x[6 * i + 5] = parent[o + b] >= 1 ? w_cpl[o + b] : 0.f;
+  }
 }
 
 // monotone float -> uint32 key (larger float, larger key)
@@ -1047,36 +1106,49 @@ int sur_get_params(sur_ctx_t* ctx, float* params) {
   return SUR_OK;
 }
 
-int sur_encode(sur_ctx_t* ctx, const int8_t* parent, const int8_t* face, const int8_t* rot, const float* w_int,
-               const float* w_cpl, const int32_t* n_bodies, int32_t n, float* X_out) {
+int sur_encode(sur_ctx_t* ctx, const int8_t* parent, const int8_t* axis, const float* R_fix, const float* p_fix,
+               const float* box_center, const float* w_int, const float* w_cpl, const int32_t* n_bodies, int32_t n,
+               float* X_out) {
   if (!ctx) return SUR_EINVAL;
-  if (n < 1 || !parent || !face || !rot || !w_int || !w_cpl || !n_bodies || !X_out)
+  if (n < 1 || !parent || !axis || !R_fix || !p_fix || !box_center || !w_int || !w_cpl || !n_bodies || !X_out)
     return fail(ctx, SUR_EINVAL, "sur_encode: bad arguments");
+  for (int32_t r = 0; r < n; ++r) {
+    const int nb = n_bodies[r];
+    if (nb < 1 || nb > kEncBodies) return fail(ctx, SUR_EINVAL, "sur_encode: n_bodies outside 1..21");
+    for (int b = 1; b < nb; ++b) {
+      const int p = parent[(size_t)r * 32 + b], a = axis[(size_t)r * 32 + b];
+      if (p < 0 || p >= b || a < 0 || a > 2) return fail(ctx, SUR_EINVAL, "sur_encode: bad parent or hinge axis");
+    }
+  }
   CK(cudaSetDevice(ctx->cfg.device));
-  int8_t *dp = nullptr, *df = nullptr, *dr = nullptr;
-  float *dwi = nullptr, *dwc = nullptr, *dX = nullptr;
+  int8_t *dp = nullptr, *da = nullptr;
+  float *dR = nullptr, *dpf = nullptr, *dc = nullptr, *dwi = nullptr, *dwc = nullptr, *dX = nullptr;
   int* dn = nullptr;
   const size_t N = (size_t)n;
-  bool ok = dalloc(&dp, N * 32) == cudaSuccess && dalloc(&df, N * 32) == cudaSuccess &&
-            dalloc(&dr, N * 32) == cudaSuccess && dalloc(&dwi, N * 32) == cudaSuccess &&
+  bool ok = dalloc(&dp, N * 32) == cudaSuccess && dalloc(&da, N * 32) == cudaSuccess &&
+            dalloc(&dR, N * 32 * 9) == cudaSuccess && dalloc(&dpf, N * 32 * 3) == cudaSuccess &&
+            dalloc(&dc, N * 32 * 3) == cudaSuccess && dalloc(&dwi, N * 32) == cudaSuccess &&
             dalloc(&dwc, N * 32) == cudaSuccess && dalloc(&dn, N) == cudaSuccess && dalloc(&dX, N * IN) == cudaSuccess;
   int rc = SUR_OK;
   if (!ok) {
     rc = fail(ctx, SUR_ENOMEM, "sur_encode: device allocation failed");
   } else {
     cudaMemcpyAsync(dp, parent, N * 32, cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(df, face, N * 32, cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(dr, rot, N * 32, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(da, axis, N * 32, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dR, R_fix, N * 32 * 9 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dpf, p_fix, N * 32 * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dc, box_center, N * 32 * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(dwi, w_int, N * 32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(dwc, w_cpl, N * 32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(dn, n_bodies, N * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
-    encode_kernel<<<n, IN, 0, ctx->stream>>>(dp, df, dr, dwi, dwc, dn, n, dX);
+    encode_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(dp, da, dR, dpf, dc, dwi, dwc, dn, n, dX);
     cudaMemcpyAsync(X_out, dX, N * IN * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) rc = fail(ctx, SUR_ECUDA, std::string("sur_encode: ") + cudaGetErrorString(e));
   }
-  cudaFree(dp); cudaFree(df); cudaFree(dr); cudaFree(dwi); cudaFree(dwc); cudaFree(dn); cudaFree(dX);
+  cudaFree(dp); cudaFree(da); cudaFree(dR); cudaFree(dpf); cudaFree(dc); cudaFree(dwi); cudaFree(dwc);
+  cudaFree(dn); cudaFree(dX);
   return rc;
 }
 

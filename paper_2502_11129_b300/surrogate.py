@@ -42,7 +42,7 @@ def lib():
         vp = C.c_void_p
         L.sur_create.argtypes = [C.POINTER(SurConfig), C.POINTER(vp)]
         L.sur_destroy.argtypes = [vp]
-        L.sur_encode.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int32, vp]
+        L.sur_encode.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int32, vp]
         L.sur_train.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, vp]
         L.sur_predict.argtypes = [vp, vp, C.c_int32, vp]
         L.sur_topk.argtypes = [vp, vp, C.c_int32, C.c_int32, vp]
@@ -103,14 +103,18 @@ class Surrogate:
     def encode(self, pop) -> np.ndarray:
         n = pop.n
         X = np.zeros((n, IN_DIM), np.float32)
-        parent = np.ascontiguousarray(pop.parent, np.int8)
-        face = np.ascontiguousarray(pop.genome_face, np.int8)
-        rot = np.ascontiguousarray(pop.genome_rot, np.int8)
-        wi = np.ascontiguousarray(pop.w_int, np.float32)
-        wc = np.ascontiguousarray(pop.w_cpl, np.float32)
+        s = pop.slots  # 32 (or 64 for long chains, which the library rejects: > 21 bodies)
+        take = slice(0, 32)
+        parent = np.ascontiguousarray(pop.parent[:, take], np.int8)
+        axis = np.ascontiguousarray(pop.axis[:, take], np.int8)
+        R_fix = np.ascontiguousarray(pop.R_fix.reshape(n, s, 9)[:, take], np.float32)
+        p_fix = np.ascontiguousarray(pop.p_fix[:, take], np.float32)
+        com = np.ascontiguousarray(pop.com[:, take], np.float32)
+        wi = np.ascontiguousarray(pop.w_int[:, take], np.float32)
+        wc = np.ascontiguousarray(pop.w_cpl[:, take], np.float32)
         nb = np.ascontiguousarray(pop.nb, np.int32)
-        self._check(lib().sur_encode(self.h, _p(parent), _p(face), _p(rot), _p(wi), _p(wc), _p(nb), n, _p(X)),
-                    "sur_encode")
+        self._check(lib().sur_encode(self.h, _p(parent), _p(axis), _p(R_fix), _p(p_fix), _p(com), _p(wi), _p(wc),
+                                     _p(nb), n, _p(X)), "sur_encode")
         return X
 
     def train(self, X, y, epochs=10, batch=1024) -> float:

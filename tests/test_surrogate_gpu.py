@@ -36,11 +36,15 @@ def ref_params(seed):
 
 def test_encoding_matches_oracle_exactly():
     M = oracle()
-    pop = P.grammar(300, seed=8)
     s = SG.Surrogate()
-    X = s.encode(pop)
-    Xr = M.encode_population(pop)
-    assert np.abs(X - Xr).max() < 1e-7
+    for pop in (P.grammar(300, seed=8), P.grammar(100, seed=9, ball_p=0.3), P.quadrupeds(4)):
+        X = s.encode(pop)
+        Xr = M.encode_population(pop)
+        # centres and axis codes exact (integer millimetres / 256, codes / 3 in FP32),
+        # weights as the FP32 copies the library receives
+        assert np.abs(X - Xr).max() < 1e-7
+        assert np.array_equal(X[:, :120].reshape(-1, 20, 6)[:, :, :3],
+                              Xr[:, :120].reshape(-1, 20, 6)[:, :, :3].astype(np.float32))
     s.close()
 
 

@@ -125,22 +125,55 @@ def test_adam_corrected_moments_are_normalised_weighted_means():
 
 
 def test_encoding_of_a_hand_built_quadruped():
+    """Zero-pose geometry written out by hand: hips (bodies 1..4) on the
+    core's +x, -x, +y, -y faces, box centres 50 + 30 mm out, hinge axes
+    vertical; knees (5..8) on each hip's outer face, centres 50 + 60 + 30 mm
+    out, hinge axes horizontal across the leg (y for the x legs, x for the y
+    legs).  All centres lie at z = 0, so the (z, x, y) order is by x, then y."""
     pop = P.quadrupeds(1)
     x = M.encode_population(pop)[0]
-    # bricks 1..4 are hips on core faces 0..3 (rotations 1, 1, 0, 0), 5..8 knees
-    # on face 0 of hips 1..4 (rotation 1); slots 9..19 empty
-    for i in range(8):
-        b = i + 1
-        assert x[5 * i] == 1.0
-        assert x[5 * i + 1] == (0 if b <= 4 else b - 4) / 20.0
-        assert x[5 * i + 2] == (b - 1 if b <= 4 else 0) / 5.0
-        assert x[5 * i + 3] == ([1, 1, 0, 0][b - 1] if b <= 4 else 1) / 3.0
-        assert x[5 * i + 4] == pop.w_int[0, b]
-    assert np.all(x[40:100] == 0.0)
-    # coupling weights: bricks 2..8 in slots 100..106; hips couple to the core -> 0
-    assert np.all(x[100:103] == 0.0)
-    assert np.allclose(x[103:107], pop.w_cpl[0, 5:9])
-    assert np.all(x[107:] == 0.0)
+    # (body, centre in mm, axis code)
+    expect = [(6, (-140, 0, 0), 2), (2, (-80, 0, 0), 3), (8, (0, -140, 0), 1), (4, (0, -80, 0), 3),
+              (3, (0, 80, 0), 3), (7, (0, 140, 0), 1), (1, (80, 0, 0), 3), (5, (140, 0, 0), 2)]
+    for i, (b, c, code) in enumerate(expect):
+        f = x[6 * i:6 * i + 6]
+        assert np.array_equal(f[:3], np.array(c) / 256.0), (i, b, f)
+        assert f[3] == code / 3.0, (i, b)
+        assert f[4] == pop.w_int[0, b]
+        # knees couple to their hip; hips hang off the core (no coupling)
+        assert f[5] == (pop.w_cpl[0, b] if b >= 5 else 0.0)
+    assert np.all(x[48:] == 0.0)
+
+
+def test_encoding_sorts_and_ignores_build_order():
+    """The same robot built in another order (bricks renumbered, parents
+    before children) encodes identically; a brick moved by one lattice step
+    moves its slot's centre by 1/256 and nothing else."""
+    pop = P.grammar(1, seed=11)
+    nb = int(pop.nb[0])
+    R9 = pop.R_fix.reshape(1, pop.slots, 9)[0]
+    x0 = M.encode(pop.parent[0], pop.axis[0], R9, pop.p_fix[0], pop.com[0], pop.w_int[0], pop.w_cpl[0], nb)
+    # renumber: a topological order of the tree that visits children in reverse
+    kids = {b: [c for c in range(1, nb) if pop.parent[0, c] == b] for b in range(nb)}
+    order, stack = [], [0]
+    while stack:
+        b = stack.pop()
+        order.append(b)
+        stack.extend(kids[b])
+    new_of = {old: new for new, old in enumerate(order)}
+    par = np.array([-1] + [new_of[pop.parent[0, o]] for o in order[1:]])
+    perm = np.array(order)
+    x1 = M.encode(par, pop.axis[0][perm], R9[perm], pop.p_fix[0][perm], pop.com[0][perm], pop.w_int[0][perm],
+                  pop.w_cpl[0][perm], nb)
+    assert np.array_equal(x0, x1)
+    # shift the centre of a leaf brick by 1 mm along its body's own x: only its slot's x, y, z change
+    leaf = max(b for b in range(1, nb) if not kids[b])
+    com = pop.com[0].copy()
+    com[leaf, 0] += 0.001
+    x2 = M.encode(pop.parent[0], pop.axis[0], R9, pop.p_fix[0], com, pop.w_int[0], pop.w_cpl[0], nb)
+    d = np.flatnonzero(x0 != x2)
+    assert 1 <= len(d) <= 3 * 6  # its own centre, and slots that swapped because of it
+    assert np.isclose(np.abs(np.sort(x0[:120]) - np.sort(x2[:120])).sum(), 1 / 256.0)
 
 
 def test_topk_against_full_sort_with_ties():
