@@ -16,8 +16,8 @@ Gaussian perturbation (sigma 0.1) of a morphology's CPG weights, clipped to
 controller if it beats the current one; morphology selection = the better
 half survives, the worse half is replaced by fresh grammar robots; the
 surrogate is retrained every generation on all (genotype, fitness) pairs
-simulated so far and screens `screen_factor` x more candidates than are
-simulated.
+simulated so far and screens `screen_factor` x more candidate controllers
+and `screen_morph` x more fresh morphologies than are simulated.
 """
 from __future__ import annotations
 
@@ -181,9 +181,12 @@ def _perturb(pop: P.Population, idx, rng, sigma, count) -> P.Population:
 
 
 def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=False, screen_factor=4,
-            epochs=10, batch=1024, seed=5, target=None, log=print, save_best=None) -> dict:
+            epochs=10, batch=1024, seed=5, target=None, log=print, save_best=None, screen_morph=4) -> dict:
     """Lamarckian memetic loop; returns the best-fitness trace with wall time
     and the number of offspring considered (evaluations) and simulated.
+    With the surrogate on, it screens screen_factor x the controller
+    variants of every morphology and screen_morph x the fresh morphologies
+    (1: fresh morphologies unscreened).
     save_best: path of an .npz that receives the final best robot (every
     Population field of it)."""
     rng = np.random.default_rng(seed)
@@ -232,7 +235,16 @@ def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=Fa
         # morphology selection: the better half survives, fresh robots replace the rest
         order = np.argsort(-best_f, kind="stable")
         keep_m = order[: n_morph // 2]
-        fresh = P.grammar(n_morph - len(keep_m), seed=seed + 1000 * (gen + 1))
+        n_fresh = n_morph - len(keep_m)
+        if surrogate and screen_morph > 1:
+            # the network ranks different morphologies far better than
+            # controller perturbations of one (cfg4): draw screen_morph x the
+            # fresh morphologies and simulate the predicted best
+            cand_m = P.grammar(n_fresh * screen_morph, seed=seed + 1000 * (gen + 1))
+            evals += cand_m.n - n_fresh
+            fresh = cand_m.subset(np.sort(sur.topk(sur.predict(sur.encode(cand_m)), n_fresh)))
+        else:
+            fresh = P.grammar(n_fresh, seed=seed + 1000 * (gen + 1))
         f_fresh = simulate(fresh, steps)
         sims += fresh.n
         evals += fresh.n
@@ -296,6 +308,7 @@ def main():
     ap.add_argument("--ctrl", type=int, default=64)
     ap.add_argument("--gens", type=int, default=30)
     ap.add_argument("--screen-factor", type=int, default=4)
+    ap.add_argument("--screen-morph", type=int, default=4)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--full-eval", action="store_true")
     a = ap.parse_args()
@@ -306,7 +319,7 @@ def main():
     else:
         plain = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=False, seed=a.seed, log=say)
         sur = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=True, screen_factor=a.screen_factor,
-                      seed=a.seed, target=plain["final_best"], log=say)
+                      seed=a.seed, target=plain["final_best"], log=say, screen_morph=a.screen_morph)
         out = dict(plain=plain, surrogate=sur)
     say(json.dumps(out))
     if _DIST is not None:

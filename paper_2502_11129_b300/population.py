@@ -23,8 +23,9 @@ Populations:
                        modules are balls (sphere geometry).
   * ``box_and_ball`` -- a core cube with one hinged ball, dropped (the
                        BOX_AND_BALL-like scene).
-  * ``rope``       -- a core cube trailing a chain of up to 25 bricks (the
-                       ARM_WITH_ROPE-like long chain within one warp).
+  * ``rope``       -- a core cube trailing a chain of up to 63 bricks (the
+                       ARM_WITH_ROPE-like long chain; beyond 25 links the
+                       simulator steps it with a block per robot).
 
 Body convention (shared reading of the model description):
   * body 0 is the core; its frame origin is the core centre.
