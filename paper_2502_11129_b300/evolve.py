@@ -181,7 +181,7 @@ def _perturb(pop: P.Population, idx, rng, sigma, count) -> P.Population:
 
 
 def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=False, screen_factor=4,
-            epochs=10, batch=1024, seed=5, target=None, log=print, save_best=None, screen_morph=4) -> dict:
+            epochs=10, batch=1024, seed=5, target=None, log=print, save_best=None, screen_morph=1) -> dict:
     """Lamarckian memetic loop; returns the best-fitness trace with wall time
     and the number of offspring considered (evaluations) and simulated.
     With the surrogate on, it screens screen_factor x the controller
@@ -308,7 +308,7 @@ def main():
     ap.add_argument("--ctrl", type=int, default=64)
     ap.add_argument("--gens", type=int, default=30)
     ap.add_argument("--screen-factor", type=int, default=4)
-    ap.add_argument("--screen-morph", type=int, default=4)
+    ap.add_argument("--screen-morph", type=int, default=1)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--full-eval", action="store_true")
     a = ap.parse_args()
