@@ -293,7 +293,7 @@ def _contact_counts(sm, n):
 
 def test_one_step_both_sweep_paths_and_the_contact_cap():
     """Robots pushed into the ground so that steps have at most 10 contacts
-    (contact-space sweep) as well as more (dof-space sweep), then the same
+    (lane-per-row sweep) as well as more (lane-per-contact sweep), then the same
     states with a cap of 6 (overflow: the 6 deepest kept in list order) --
     each against the oracle."""
     pop = P.grammar(128, seed=61)
@@ -310,6 +310,21 @@ def test_one_step_both_sweep_paths_and_the_contact_cap():
     assert over.sum() >= 20 and (nc <= 6).all()
     assert np.array_equal(over, (r.status_ref & S.ST_OVERFLOW) != 0)
     _check("cap-6", r, y)
+
+
+def test_one_step_three_sweep_paths():
+    """Large robots pushed deep into the ground so that the three formulations
+    of the sweep all run in one launch: at most 10 contacts (contact space,
+    lane = row), 11 to 32 (contact space, lane = contact, Delassus blocks in
+    the scratch) and more (dof space) -- every robot against the oracle."""
+    pop = P.grammar(48, seed=71, hinges=(20, 25))
+    q, v, s = P.random_state(pop, seed=72, angle=0.3)
+    q[:, 2] = pop.q0[:, 2] + np.random.default_rng(73).uniform(-0.08, -0.03, pop.n)
+    r, y, gst, sm = _one_step(pop, q, v, s)
+    nc = _contact_counts(sm, pop.n)
+    print("contact counts", np.bincount(nc))
+    assert (nc <= 10).sum() >= 5 and ((nc > 10) & (nc <= 32)).sum() >= 5 and (nc > 32).sum() >= 5, nc
+    _check("three-sweeps", r, y)
 
 
 def test_empty_and_ragged_inputs():
