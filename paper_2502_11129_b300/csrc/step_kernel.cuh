@@ -85,7 +85,9 @@ __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFul
 // (PTX rsqrt.approx.ftz.f32, a few ulp): without the flush the compiler adds
 // a subnormal fix-up, which lengthens the Gauss-Seidel update's dependency
 // chain by ~15 cycles.  Used for the friction-disk scale min(1, mu l_n / |l_t|),
-// where a flushed |l_t|^2 < 1e-38 changes nothing measurable.
+// the Cholesky pivots and the quaternion normalisation, where flushing an
+// argument below 1e-38 changes nothing measurable (pivots of a mass matrix
+// and unit quaternions are far from it).
 __device__ __forceinline__ float rsqrt_ftz(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -808,8 +810,10 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         const float mij = (row && lane >= j) ? Li[j] - (s0 + s1) : 0.f;
         const float piv = shf(mij, j);
         if (!(piv > 0.f)) { chol_ok = false; break; }
-        const float d = sqrtf(piv);
-        const float inv = 1.f / d;
+        // the pivot's root and its reciprocal from one SFU reciprocal square
+        // root (the rounded square root and division sit on the column chain)
+        const float inv = rsqrt_ftz(piv);
+        const float d = piv * inv;
         if (lane == j) { sm.M[tri(j) + j] = d; sm.invd[j] = inv; }
         if (row && lane > j) sm.M[tri(lane) + j] = mij * inv;
         __syncwarp();
@@ -1216,11 +1220,12 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     const float np0x = p0x + dt * vx, np0y = p0y + dt * vy, np0z = p0z + dt * vz;
     float dq0 = 1.f, dq1 = 0.f, dq2 = 0.f, dq3 = 0.f;
     {
-      const float nw = sqrtf(ox * ox + oy * oy + oz * oz);
-      if (nw >= 1e-12f) {
+      const float w2 = ox * ox + oy * oy + oz * oz;
+      if (w2 >= 1e-24f) {  // |w| >= 1e-12, else the identity
+        const float inw = rsqrt_ftz(w2);
         float sa, ca;
-        sincosf(0.5f * dt * nw, &sa, &ca);
-        sa = sa / nw;
+        sincosf(0.5f * dt * (w2 * inw), &sa, &ca);
+        sa *= inw;
         dq0 = ca; dq1 = sa * ox; dq2 = sa * oy; dq3 = sa * oz;
       }
     }
@@ -1228,8 +1233,8 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
     float r1 = qw * dq1 + qx * dq0 + qy * dq3 - qz * dq2;
     float r2 = qw * dq2 - qx * dq3 + qy * dq0 + qz * dq1;
     float r3 = qw * dq3 + qx * dq2 - qy * dq1 + qz * dq0;
-    const float nr = sqrtf(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
-    r0 /= nr; r1 /= nr; r2 /= nr; r3 /= nr;
+    const float inr = rsqrt_ftz(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    r0 *= inr; r1 *= inr; r2 *= inr; r3 *= inr;
     const float thp = shf(vplus, (5 + lane) & 31);
     const float ntheta = hinge ? theta + dt * thp : 0.f;
     bool bad = !(isfinite(np0x) && isfinite(np0y) && isfinite(np0z) && isfinite(r0) && isfinite(r1) &&
