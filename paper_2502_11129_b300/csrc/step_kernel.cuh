@@ -304,15 +304,24 @@ static __device__ __noinline__ float lane_contact_sweep(float4* lamS, const floa
   const float4* A4 = reinterpret_cast<const float4*>(Ag) + 3 * lane;
   const int kstride = 3 * nc;  // float4 between block rows k and k + 1
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  // blocks of the current contact and the next one (prefetch distance 2)
-  float4 p0 = mine ? A4[0] : z4, p1 = mine ? A4[1] : z4, p2 = mine ? A4[2] : z4;
-  float4 q0 = mine ? A4[kstride] : z4, q1 = mine ? A4[kstride + 1] : z4, q2 = mine ? A4[kstride + 2] : z4;
+  // Three register sets hold the blocks of the current contact, the next one
+  // and the one after (prefetch distance 2); the loop is unrolled by three so
+  // that the sets rotate by name instead of by register moves.
+  struct Blk {
+    float4 x, y, z;
+  };
+  Blk A = {mine ? A4[0] : z4, mine ? A4[1] : z4, mine ? A4[2] : z4};
+  Blk B = {mine ? A4[kstride] : z4, mine ? A4[kstride + 1] : z4, mine ? A4[kstride + 2] : z4};
+  Blk C;
   const int nupd = iters * nc;
   int k = 0, k2 = 2;  // contact of this update, and of the block loaded now
-#pragma unroll 1
-  for (int upd = 0; upd < nupd; ++upd) {
+  // one update with the block of contact k in `cur`; the block of contact k2
+  // is loaded into `load`
+  auto update = [&](const Blk& cur, Blk& load) {
     const float4* An = A4 + (size_t)kstride * k2;
-    const float4 r0 = mine ? An[0] : z4, r1 = mine ? An[1] : z4, r2 = mine ? An[2] : z4;
+    load.x = mine ? An[0] : z4;
+    load.y = mine ? An[1] : z4;
+    load.z = mine ? An[2] : z4;
     const float lnn = fmaxf(0.f, fmaf(-gn, wn, an * ln));
     const float dn = lnn - ln;
     const float l1t = fmaf(-b1, dn, fmaf(-g1, w1, a1 * l1));
@@ -325,14 +334,20 @@ static __device__ __noinline__ float lane_contact_sweep(float4* lamS, const floa
       l1 = l1t * sc;
       l2 = l2t * sc;
     }
-    // block (k, lane) row-major in p0..p2: (a00 a01 a02 a10) (a11 a12 a20 a21) (a22 . . .)
-    wn = fmaf(p0.z, D2, fmaf(p0.y, D1, fmaf(p0.x, Dn, wn)));
-    w1 = fmaf(p1.y, D2, fmaf(p1.x, D1, fmaf(p0.w, Dn, w1)));
-    w2 = fmaf(p2.x, D2, fmaf(p1.w, D1, fmaf(p1.z, Dn, w2)));
-    p0 = q0; p1 = q1; p2 = q2;
-    q0 = r0; q1 = r1; q2 = r2;
+    // block (k, lane) row-major: (a00 a01 a02 a10) (a11 a12 a20 a21) (a22 . . .)
+    wn = fmaf(cur.x.z, D2, fmaf(cur.x.y, D1, fmaf(cur.x.x, Dn, wn)));
+    w1 = fmaf(cur.y.y, D2, fmaf(cur.y.x, D1, fmaf(cur.x.w, Dn, w1)));
+    w2 = fmaf(cur.z.x, D2, fmaf(cur.y.w, D1, fmaf(cur.y.z, Dn, w2)));
     k = k + 1 < nc ? k + 1 : 0;
     k2 = k2 + 1 < nc ? k2 + 1 : 0;
+  };
+#pragma unroll 1
+  for (int upd = 0; upd < nupd; upd += 3) {
+    update(A, C);
+    if (upd + 1 >= nupd) break;
+    update(B, A);
+    if (upd + 2 >= nupd) break;
+    update(C, B);
   }
   if (mine) lamS[lane] = make_float4(ln, l1, l2, 0.f);
   __syncwarp();
