@@ -127,6 +127,20 @@ __host__ __device__ __forceinline__ void quat_to_R(float qw, float qx, float qy,
   R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
 }
 
+// 1/sqrt(x) from the special-function unit with subnormals flushed to zero
+// (PTX rsqrt.approx.ftz.f32, a few ulp): without the flush the compiler adds
+// a subnormal fix-up, which lengthens the Gauss-Seidel update's dependency
+// chain by ~15 cycles.  Used for the friction-disk scale min(1, mu l_n / |l_t|),
+// the Cholesky pivots, the quaternion normalisation and the separating-axis
+// directions, where flushing an argument below 1e-38 changes nothing
+// measurable (all of them are far from it, or have a threshold above it).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+
 template <int NS = 32>
 __host__ __device__ __forceinline__ void axis_of(const float (*R)[NS], int b, int k, float* o) {
   o[0] = R[k][b]; o[1] = R[3 + k][b]; o[2] = R[6 + k][b];
@@ -181,9 +195,20 @@ __host__ __device__ __noinline__ int box_box_lane(const float (*RR)[NS], const f
       pick(Ax, (e - 6) / 3, ai);
       pick(Bx, (e - 6) % 3, bj);
       cross3(ai, bj, L);
+#ifdef __CUDA_ARCH__
+      // one SFU reciprocal square root instead of a rounded square root and
+      // three divisions (nine edge axes per pair, on one lane's chain)
+      const float l2 = dot3(L, L);
+      if (l2 < 1e-12f) valid = false;
+      else {
+        const float il = rsqrt_ftz(l2);
+        L[0] *= il; L[1] *= il; L[2] *= il;
+      }
+#else
       const float nl = sqrtf(dot3(L, L));
       if (nl < 1e-6f) valid = false;
       else { L[0] /= nl; L[1] /= nl; L[2] /= nl; }
+#endif
     }
     if (valid) {
       float rA = 0.f, rB = 0.f;

@@ -81,19 +81,6 @@ static_assert(16 * (sizeof(WarpSmem) + 1024) <= 164 * 1024, "per-warp shared mem
 
 __device__ __forceinline__ float shf(float x, int src) { return __shfl_sync(kFull, x, src); }
 
-// 1/sqrt(x) from the special-function unit with subnormals flushed to zero
-// (PTX rsqrt.approx.ftz.f32, a few ulp): without the flush the compiler adds
-// a subnormal fix-up, which lengthens the Gauss-Seidel update's dependency
-// chain by ~15 cycles.  Used for the friction-disk scale min(1, mu l_n / |l_t|),
-// the Cholesky pivots and the quaternion normalisation, where flushing an
-// argument below 1e-38 changes nothing measurable (pivots of a mass matrix
-// and unit quaternions are far from it).
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 // Double-float arithmetic (Dekker 1971 products, Knuth two-sum): a value is
 // h + l in FP32 with |l| <= ulp(h) / 2, about 44 bits.  The round-to-nearest
 // intrinsics keep the compiler from fusing the error-free steps into FMAs.
