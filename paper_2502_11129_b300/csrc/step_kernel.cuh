@@ -1048,11 +1048,13 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       __syncwarp();
     }
     // tangent/normal coupling A_tn = Y_t . Y_n of each contact (lane =
-    // contact), and for the dof-space sweep (more than 10 contacts) the block
-    // B_k = Y_(k+1) Y_k^T to the next contact in sweep order
+    // contact), and for the dof-space sweep (more than 32 contacts) the block
+    // B_k = Y_(k+1) Y_k^T to the next contact in sweep order; up to 10
+    // contacts the sweep reads the couplings from the Delassus matrix it
+    // builds
     const bool dofspace = nc > kLaneContacts;
 #pragma unroll 1
-    for (int k0 = 0; k0 < nc; k0 += 32) {
+    for (int k0 = 0; 3 * nc > 32 && k0 < nc; k0 += 32) {
       const int k = k0 + lane;
       if (k < nc) {
         const float4* yn = reinterpret_cast<const float4*>(Yg + (size_t)(3 * k) * 32);
@@ -1149,10 +1151,12 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       float4* cS = lamS + 12;
       if (lane < nc) {
         const float4* c4 = reinterpret_cast<const float4*>(cstg) + 6 * lane;
-        // (b_n, g_n, R_n, b_t1), (g_t1, R_t1, b_t2, g_t2), (R_t2, A_t1n, A_t2n, 0)
+        // (b_n, g_n, R_n, b_t1), (g_t1, R_t1, b_t2, g_t2), (R_t2, ., ., .)
         const float4 x0 = c4[0], x1 = c4[1], x2 = c4[2];
+        // A_t1n, A_t2n: column 3k of rows 3k + 1, 3k + 2 of A ([column][row] above)
+        const float at1n = sm.Yt[3 * lane][3 * lane + 1], at2n = sm.Yt[3 * lane][3 * lane + 2];
         cS[2 * lane] = make_float4(x0.y, fmaf(-x0.z, x0.y, 1.f), x1.x, fmaf(-x1.y, x1.x, 1.f));
-        cS[2 * lane + 1] = make_float4(x1.x * x2.y, x1.w, fmaf(-x2.x, x1.w, 1.f), x1.w * x2.z);
+        cS[2 * lane + 1] = make_float4(x1.x * at1n, x1.w, fmaf(-x2.x, x1.w, 1.f), x1.w * at2n);
         lamS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();

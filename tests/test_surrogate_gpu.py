@@ -190,4 +190,11 @@ def test_argument_errors():
         s.topk(np.zeros(10, np.float32), 20)
     with pytest.raises(SG.SurrogateError, match="SUR_EINVAL"):
         s.gradients(np.zeros((SG.MAX_BATCH + 1, 128), np.float32), np.zeros(SG.MAX_BATCH + 1, np.float32))
+    # the encoding covers robots of up to 21 bodies (20 brick slots), parents before children
+    with pytest.raises(SG.SurrogateError, match="n_bodies"):
+        s.encode(P.rope(2, seed=1, links=24))
+    bad = P.grammar(2, seed=3)
+    bad.parent[1, 2] = 5  # body 2 hanging from a later body
+    with pytest.raises(SG.SurrogateError, match="parent"):
+        s.encode(bad)
     s.close()
