@@ -615,15 +615,40 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int t = 0; t < 9; ++t) Fr[t] = fld(F_RFIX + t);
 #pragma unroll
       for (int t = 0; t < 3; ++t) Fp[t] = fld(F_PFIX + t);
+      // A lattice joint rotation (every column one entry +-1, the others 0)
+      // turns the row-times-matrix product into a signed pick of one entry
+      // per column, which is what the double-float products give exactly (a
+      // normalised pair times +-1 or 0, plus zeros): taken when every body of
+      // the robot has one.
+      int rc[3];
+      float sg[3];
+      bool lat = true;
+#pragma unroll
+      for (int col = 0; col < 3; ++col) {
+        const float a0 = Fr[col], a1 = Fr[3 + col], a2 = Fr[6 + col];
+        rc[col] = a0 != 0.f ? 0 : (a1 != 0.f ? 1 : 2);
+        sg[col] = a0 + a1 + a2;
+        const int nz = (a0 != 0.f) + (a1 != 0.f) + (a2 != 0.f);
+        lat = lat && nz == 1 && fabsf(sg[col]) == 1.f;
+      }
+      const bool lattice = __all_sync(kFull, lat);
 #pragma unroll 1
       for (int lvl = 1; lvl <= maxdepth; ++lvl) {
         const f2 p0 = f2_shf(hz0, par0), p1 = f2_shf(hz1, par0), p2 = f2_shf(hz2, par0), pb = f2_shf(hzb, par0);
         if (depth == lvl) {
           // (third row of R_parent) x R_fix, then the hinge rotation mixes columns i, j
           f2 t[3];
+          if (lattice) {
 #pragma unroll
-          for (int col = 0; col < 3; ++col)
-            t[col] = f2_add(f2_add(f2_mulf(p0, Fr[col]), f2_mulf(p1, Fr[3 + col])), f2_mulf(p2, Fr[6 + col]));
+            for (int col = 0; col < 3; ++col) {
+              const f2 pc = rc[col] == 0 ? p0 : (rc[col] == 1 ? p1 : p2);
+              t[col] = {pc.h * sg[col], pc.l * sg[col]};
+            }
+          } else {
+#pragma unroll
+            for (int col = 0; col < 3; ++col)
+              t[col] = f2_add(f2_add(f2_mulf(p0, Fr[col]), f2_mulf(p1, Fr[3 + col])), f2_mulf(p2, Fr[6 + col]));
+          }
           const f2 ti = k == 0 ? t[1] : (k == 1 ? t[2] : t[0]);
           const f2 tj = k == 0 ? t[2] : (k == 1 ? t[0] : t[1]);
           const f2 tk = k == 0 ? t[0] : (k == 1 ? t[1] : t[2]);
