@@ -1194,8 +1194,10 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int it = 0; it < P.iters; ++it) {
         const float4 l0 = lamS[0];
         float ln = l0.x, l1 = l0.y, l2 = l0.z;  // impulses of the contact being updated
-#pragma unroll 1
-        for (int k = 0; k < nc; ++k) {
+        float mn, m1, m2;                        // and of the next one
+        // update of contact k from its impulses (ln, l1, l2); the next
+        // contact's impulses are read into (bn_, b1_, b2_)
+        auto update = [&](int k, float ln, float l1, float l2, float& bn_, float& b1_, float& b2_) {
           const int r = 3 * k;
           // this contact's constants and this lane's row of A in its columns
           // (loaded first, used after the shuffles), the next one's impulses
@@ -1214,9 +1216,16 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
           const float d1 = fmaf(l1t, sc, -l1), d2 = fmaf(l2t, sc, -l2);
           w = fmaf(a2, d2, fmaf(a1, d1, wd));
           lamS[k] = make_float4(lnn, l1t * sc, l2t * sc, 0.f);
-          ln = nl.x;
-          l1 = nl.y;
-          l2 = nl.z;
+          bn_ = nl.x;
+          b1_ = nl.y;
+          b2_ = nl.z;
+        };
+        // two contacts per pass, so that the impulse registers alternate by name
+#pragma unroll 1
+        for (int k = 0; k < nc; k += 2) {
+          update(k, ln, l1, l2, mn, m1, m2);
+          if (k + 1 >= nc) break;
+          update(k + 1, mn, m1, m2, ln, l1, l2);
         }
       }
       __syncwarp();
