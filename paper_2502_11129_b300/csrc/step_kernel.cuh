@@ -826,11 +826,22 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
         const float* Lj = sm.M + tri(j);
         float s0 = 0.f, s1 = 0.f;
         if (row && lane >= j) {
+          // four terms an iteration with their loads first (one load latency
+          // per four terms); even terms to s0, odd to s1, in order
           int k = 0;
 #pragma unroll 1
-          for (; k + 1 < j; k += 2) {
+          for (; k + 3 < j; k += 4) {
+            const float a0 = Li[k], b0 = Lj[k], a1 = Li[k + 1], b1 = Lj[k + 1];
+            const float a2 = Li[k + 2], b2 = Lj[k + 2], a3 = Li[k + 3], b3 = Lj[k + 3];
+            s0 += a0 * b0;
+            s1 += a1 * b1;
+            s0 += a2 * b2;
+            s1 += a3 * b3;
+          }
+          if (k + 1 < j) {
             s0 += Li[k] * Lj[k];
             s1 += Li[k + 1] * Lj[k + 1];
+            k += 2;
           }
           if (k < j) s0 += Li[k] * Lj[k];
         }
@@ -1020,18 +1031,26 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       // J_r into this lane's column of Yt ([dof][row]); compact loops keep the code small
       float* yr = &sm.Yt[0][lane];
       float jv = 0.f;
+      // two dofs an iteration with their loads first; an odd last dof is
+      // formed twice and counted once
+      auto jcoef = [&](int j) {
+        if (j < 6) return sroot;
+        const int bj = j - 5;
+        return (float)((int)((pa >> bj) & 1u) - (int)((pb >> bj) & 1u));
+      };
 #pragma unroll 1
-      for (int j = 0; j < nv; ++j) {
-        float coef;
-        if (j < 6) coef = sroot;
-        else {
-          const int bj = j - 5;
-          coef = (float)((int)((pa >> bj) & 1u) - (int)((pb >> bj) & 1u));
-        }
-        const float Jj = coef * (sm.S[0][j] * wa[0] + sm.S[1][j] * wa[1] + sm.S[2][j] * wa[2] + sm.S[3][j] * d[0] +
-                                 sm.S[4][j] * d[1] + sm.S[5][j] * d[2]);
-        jv += Jj * sm.vfree[j];
-        yr[32 * j] = Jj;
+      for (int j = 0; j < nv; j += 2) {
+        const int j1 = j + 1 < nv ? j + 1 : j;
+        float Sa[6], Sb[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) { Sa[q] = sm.S[q][j]; Sb[q] = sm.S[q][j1]; }
+        const float va = sm.vfree[j], vb = sm.vfree[j1];
+        const float Ja = jcoef(j) * (Sa[0] * wa[0] + Sa[1] * wa[1] + Sa[2] * wa[2] + Sa[3] * d[0] + Sa[4] * d[1] + Sa[5] * d[2]);
+        const float Jb = jcoef(j1) * (Sb[0] * wa[0] + Sb[1] * wa[1] + Sb[2] * wa[2] + Sb[3] * d[0] + Sb[4] * d[1] + Sb[5] * d[2]);
+        jv += Ja * va;
+        if (j1 != j) jv += Jb * vb;
+        yr[32 * j] = Ja;
+        yr[32 * j1] = Jb;
       }
 #pragma unroll 1
       for (int j = nv; j < 32; ++j) yr[32 * j] = 0.f;
@@ -1041,11 +1060,20 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       for (int i = 0; i < nv; ++i) {
         const float* Li = sm.M + tri(i);
         float t0 = yr[32 * i], t1 = 0.f;
-        int kk = 0;
+        int kk = 0;  // four terms an iteration, loads first; even terms to t0, odd to t1
 #pragma unroll 1
-        for (; kk + 1 < i; kk += 2) {
+        for (; kk + 3 < i; kk += 4) {
+          const float a0 = Li[kk], b0 = yr[32 * kk], a1 = Li[kk + 1], b1 = yr[32 * (kk + 1)];
+          const float a2 = Li[kk + 2], b2 = yr[32 * (kk + 2)], a3 = Li[kk + 3], b3 = yr[32 * (kk + 3)];
+          t0 -= a0 * b0;
+          t1 -= a1 * b1;
+          t0 -= a2 * b2;
+          t1 -= a3 * b3;
+        }
+        if (kk + 1 < i) {
           t0 -= Li[kk] * yr[32 * kk];
           t1 -= Li[kk + 1] * yr[32 * (kk + 1)];
+          kk += 2;
         }
         if (kk < i) t0 -= Li[kk] * yr[32 * kk];
         const float yi = (t0 + t1) * sm.invd[i];
@@ -1054,7 +1082,7 @@ step_kernel(const float* __restrict__ mf, const int* __restrict__ mi, const int4
       }
       if (act) {
         float4* dst = reinterpret_cast<float4*>(Yg + (size_t)row * 32);
-#pragma unroll 1
+#pragma unroll 2
         for (int i = 0; i < 8; ++i)
           dst[i] = make_float4(yr[32 * (4 * i)], yr[32 * (4 * i + 1)], yr[32 * (4 * i + 2)], yr[32 * (4 * i + 3)]);
         // softness kappa A (mass-normalised CFM), floored at min_cfm: a row the
