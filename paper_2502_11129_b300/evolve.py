@@ -181,27 +181,35 @@ def _perturb(pop: P.Population, idx, rng, sigma, count) -> P.Population:
 
 
 def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=False, screen_factor=4,
-            epochs=10, batch=1024, seed=5, target=None, log=print, save_best=None, screen_morph=1) -> dict:
+            epochs=10, batch=1024, seed=5, target=None, log=print, save_best=None, screen_morph=1,
+            relative=False) -> dict:
     """Lamarckian memetic loop; returns the best-fitness trace with wall time
     and the number of offspring considered (evaluations) and simulated.
     With the surrogate on, it screens screen_factor x the controller
     variants of every morphology and screen_morph x the fresh morphologies
     (1: fresh morphologies unscreened).
+    relative: the network learns an offspring's fitness minus its parent's
+    (the morphology's best when the offspring was drawn), from the simulated
+    offspring only, so that its capacity goes to the differences between
+    siblings, which is all the screening ranks; until it has data, the
+    loop simulates unscreened offspring.
     save_best: path of an .npz that receives the final best robot (every
     Population field of it)."""
+    if relative and screen_morph > 1:
+        raise ValueError("relative targets rank siblings only: screen_morph must be 1")
     rng = np.random.default_rng(seed)
     morphs = P.grammar(n_morph, seed=seed)
     best_f = simulate(morphs, steps)
     sur = SG.Surrogate(seed=seed, device=_DEVICE) if surrogate else None
-    data_X = [sur.encode(morphs)] if surrogate else []
-    data_y = [best_f.copy()]
+    data_X = [sur.encode(morphs)] if surrogate and not relative else []
+    data_y = [best_f.copy()] if not relative else []
     trace = RunLog([float(best_f.max())], [n_morph], [n_morph], [0.0])
     t0 = time.perf_counter()
     evals = n_morph
     sims = n_morph
     reached = None
     for gen in range(gens):
-        if surrogate:
+        if surrogate and data_y:
             X_all = np.concatenate(data_X)
             y_all = np.concatenate(data_y).astype(np.float32)
             sur.train(X_all, y_all, epochs=epochs, batch=min(batch, len(y_all)))
@@ -222,7 +230,7 @@ def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=Fa
         sims += offspring.n
         if surrogate:
             data_X.append(sur.encode(offspring))
-            data_y.append(f)
+            data_y.append(f - np.repeat(best_f, n_ctrl) if relative else f)
         # Lamarckian write-back of the best controller of each morphology
         fm = f.reshape(n_morph, n_ctrl)
         arg = fm.argmax(axis=1)
@@ -248,7 +256,7 @@ def memetic(n_morph=256, n_ctrl=64, gens=30, steps=5000, sigma=0.1, surrogate=Fa
         f_fresh = simulate(fresh, steps)
         sims += fresh.n
         evals += fresh.n
-        if surrogate:
+        if surrogate and not relative:
             data_X.append(sur.encode(fresh))
             data_y.append(f_fresh)
         kept = morphs.subset(keep_m)
@@ -309,6 +317,7 @@ def main():
     ap.add_argument("--gens", type=int, default=30)
     ap.add_argument("--screen-factor", type=int, default=4)
     ap.add_argument("--screen-morph", type=int, default=1)
+    ap.add_argument("--relative", action="store_true", help="train the screening network on fitness minus the parent's")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--full-eval", action="store_true")
     a = ap.parse_args()
@@ -319,7 +328,8 @@ def main():
     else:
         plain = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=False, seed=a.seed, log=say)
         sur = memetic(a.morph, a.ctrl, a.gens, a.steps, surrogate=True, screen_factor=a.screen_factor,
-                      seed=a.seed, target=plain["final_best"], log=say, screen_morph=a.screen_morph)
+                      seed=a.seed, target=plain["final_best"], log=say, screen_morph=a.screen_morph,
+                      relative=a.relative)
         out = dict(plain=plain, surrogate=sur)
     say(json.dumps(out))
     if _DIST is not None:

@@ -2,7 +2,8 @@
 
 Gain test: offspring chosen by the trained surrogate simulate to higher
 fitness than offspring chosen at random (one-sided Mann-Whitney p < 0.01).
-The memetic loop runs end to end with the surrogate on and off.
+The memetic loop runs end to end with the surrogate on and off, and with
+relative targets.
 """
 import numpy as np
 import pytest
@@ -28,6 +29,19 @@ def test_memetic_loop_runs_with_and_without_surrogate():
     assert plain["best"][-1] >= plain["best"][0]  # Lamarckian write-back never loses the best
     assert sur["evals"][-1] > plain["evals"][-1]  # the surrogate considers more offspring per simulation
     assert sur["sims"][-1] == plain["sims"][-1]
+
+
+def test_memetic_loop_with_relative_targets():
+    """Relative targets: the first generation has no training data and
+    simulates unscreened offspring drawn as the plain loop draws them (the
+    same best); later generations screen."""
+    plain = E.memetic(n_morph=16, n_ctrl=8, gens=3, steps=300, surrogate=False, seed=4, log=lambda *a: None)
+    rel = E.memetic(n_morph=16, n_ctrl=8, gens=3, steps=300, surrogate=True, screen_factor=4, seed=4,
+                    relative=True, log=lambda *a: None)
+    assert rel["best"][1] == plain["best"][1]
+    assert rel["evals"][1] == plain["evals"][1]
+    assert rel["evals"][-1] > plain["evals"][-1] and rel["sims"][-1] == plain["sims"][-1]
+    assert rel["best"][-1] >= rel["best"][0]
 
 
 def test_rank_helpers_match_library():
